@@ -1,0 +1,372 @@
+/*
+ * sip_oracle.c -- CPU oracle for Stone's strongly implicit procedure (SIP).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  It shares
+ * no code, header, table or constant with the CUDA path in
+ * paper_1303_4538_gb300/csrc, and neither side includes or links the other.
+ *
+ * What it computes (paper: Scheit, Hager, Treibig, Becker, Wellein,
+ * "Optimization of FASTEST-3D for Modern Multicore Systems", arXiv:1303.4538):
+ *   the linear solver of every equation system in FASTEST is Stone's SIP, an
+ *   iteration built on an incomplete LU factorisation (Sec. 1 and Sec. 4.1,
+ *   routines lu3d / resforward3d / backward3d of Tables 1-4).  The paper does
+ *   not restate Stone's equations; the reading used here is the standard
+ *   3-D 7-point SIP with one constant alpha (Stone 1968, the paper's ref. [HLS68]):
+ *
+ *   Factorisation (lu3d), for every cell P after its lower neighbours W,S,B:
+ *     LB = AB / (1 + alpha (UN_B + UE_B))
+ *     LW = AW / (1 + alpha (UN_W + UT_W))
+ *     LS = AS / (1 + alpha (UE_S + UT_S))
+ *     P1 = alpha (LB UN_B + LW UN_W)
+ *     P2 = alpha (LB UE_B + LS UE_S)
+ *     P3 = alpha (LW UT_W + LS UT_S)
+ *     LP = AP + P1 + P2 + P3 - LB UT_B - LW UE_W - LS UN_S
+ *     UN = (AN - P1) / LP,  UE = (AE - P2) / LP,  UT = (AT - P3) / LP
+ *   so that L U = A + N, where N cancels (up to alpha) the six fill entries of
+ *   L U by linear extrapolation from the two stencil neighbours that flank
+ *   each fill position.
+ *
+ *   Iteration (resforward3d then backward3d):
+ *     r = b - A x                             (residual; norm of r)
+ *     y_P = (r_P - LB y_B - LW y_W - LS y_S) / LP   ascending cells
+ *     d_P = y_P - UE d_E - UN d_N - UT d_T           descending cells
+ *     x <- x + d
+ *
+ * Conventions:
+ *   - natural layout p = i + nx*(j + ny*k), 0-based, i fastest;
+ *   - lower neighbours W=(i-1,j,k), S=(i,j-1,k), B=(i,j,k-1), upper E,N,T;
+ *   - A holds matrix entries: AP > 0 on the diagonal, AW..AT <= 0;
+ *     the paper's Listing 1 uses the FV sign (ap fi = sum a_nb fi_nb + su),
+ *     so A_nb = -a_nb, AP = ap, b = su;
+ *   - a neighbour outside the block does not exist: it is skipped, never
+ *     read, and its coefficient is ignored (the flat index is never used to
+ *     reach across a face);
+ *   - residual norm: Euclidean, relres = ||b - A x||_2 / ||b||_2 (||b|| = 0
+ *     gives relres = ||r||_2).  The paper does not fix the norm.
+ *   - sums of squares use Neumaier compensated summation in double so the
+ *     result does not depend on the host (build with -ffp-contract=off).
+ *
+ * Parity status: the factorisation is pinned by the defining identity
+ * L U = A + N, by alpha = 0 (ILU(0)) and by the 1-D case (exact LU); the
+ * iteration by the dense preconditioned-Richardson step and by convergence to
+ * the dense solution; the single-precision and refinement drivers by
+ * convergence to the FP64 solution.  No value printed in the paper can be
+ * matched (it prints none for SIP).
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ID(i, j, k) ((size_t)(i) + (size_t)nx * ((size_t)(j) + (size_t)ny * (size_t)(k)))
+
+/* ------------------------------------------------------------------ */
+/* compensated sum of squares                                           */
+typedef struct { double s, c; } nsum;
+static void nsum_add(nsum *a, double v) {
+  double t = a->s + v;
+  if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
+  else a->c += (v - t) + a->s;
+  a->s = t;
+}
+static double nsum_get(const nsum *a) { return a->s + a->c; }
+
+double oracle_dot_sq(int64_t n, const double *v) {
+  nsum a = {0.0, 0.0};
+  for (int64_t p = 0; p < n; ++p) nsum_add(&a, v[p] * v[p]);
+  return nsum_get(&a);
+}
+
+/* ------------------------------------------------------------------ */
+/* Stone factorisation (lu3d), FP64.  Returns 0, or -1 - p for the first
+ * cell p where a divisor is zero or a result is not finite (breakdown). */
+int oracle_factor(int nx, int ny, int nz, double alpha,
+                  const double *ap, const double *aw, const double *ae, const double *as,
+                  const double *an, const double *ab, const double *at,
+                  double *lb, double *lw, double *ls, double *lp,
+                  double *un, double *ue, double *ut) {
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t p = ID(i, j, k);
+        double unB = 0, ueB = 0, utB = 0, unW = 0, ueW = 0, utW = 0, unS = 0, ueS = 0, utS = 0;
+        double LB = 0, LW = 0, LS = 0;
+        if (k > 0) {
+          size_t q = ID(i, j, k - 1);
+          unB = un[q]; ueB = ue[q]; utB = ut[q];
+          double den = 1.0 + alpha * (unB + ueB);
+          if (den == 0.0) return -1 - (int)p;
+          LB = ab[p] / den;
+        }
+        if (i > 0) {
+          size_t q = ID(i - 1, j, k);
+          unW = un[q]; ueW = ue[q]; utW = ut[q];
+          double den = 1.0 + alpha * (unW + utW);
+          if (den == 0.0) return -1 - (int)p;
+          LW = aw[p] / den;
+        }
+        if (j > 0) {
+          size_t q = ID(i, j - 1, k);
+          unS = un[q]; ueS = ue[q]; utS = ut[q];
+          double den = 1.0 + alpha * (ueS + utS);
+          if (den == 0.0) return -1 - (int)p;
+          LS = as[p] / den;
+        }
+        double P1 = alpha * (LB * unB + LW * unW);
+        double P2 = alpha * (LB * ueB + LS * ueS);
+        double P3 = alpha * (LW * utW + LS * utS);
+        double LP = ap[p] + P1 + P2 + P3 - LB * utB - LW * ueW - LS * unS;
+        if (LP == 0.0 || !isfinite(LP)) return -1 - (int)p;
+        lb[p] = LB; lw[p] = LW; ls[p] = LS; lp[p] = LP;
+        /* an upper neighbour outside the block has no entry in U */
+        un[p] = (j + 1 < ny) ? (an[p] - P1) / LP : 0.0;
+        ue[p] = (i + 1 < nx) ? (ae[p] - P2) / LP : 0.0;
+        ut[p] = (k + 1 < nz) ? (at[p] - P3) / LP : 0.0;
+        if (!isfinite(LB) || !isfinite(LW) || !isfinite(LS) || !isfinite(un[p]) ||
+            !isfinite(ue[p]) || !isfinite(ut[p]))
+          return -1 - (int)p;
+      }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* residual r = b - A x (general 7-point matrix); returns sum r^2.     */
+double oracle_residual(int nx, int ny, int nz,
+                       const double *ap, const double *aw, const double *ae, const double *as,
+                       const double *an, const double *ab, const double *at,
+                       const double *b, const double *x, double *r) {
+  nsum acc = {0.0, 0.0};
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t p = ID(i, j, k);
+        double ax = ap[p] * x[p];
+        if (i > 0) ax += aw[p] * x[ID(i - 1, j, k)];
+        if (i + 1 < nx) ax += ae[p] * x[ID(i + 1, j, k)];
+        if (j > 0) ax += as[p] * x[ID(i, j - 1, k)];
+        if (j + 1 < ny) ax += an[p] * x[ID(i, j + 1, k)];
+        if (k > 0) ax += ab[p] * x[ID(i, j, k - 1)];
+        if (k + 1 < nz) ax += at[p] * x[ID(i, j, k + 1)];
+        double rp = b[p] - ax;
+        if (r) r[p] = rp;
+        nsum_add(&acc, rp * rp);
+      }
+  return nsum_get(&acc);
+}
+
+/* Residual of a symmetric matrix in the form of the paper's Listing 1:
+ * only the east, north and top coefficients are read; the west, south and
+ * bottom entries of row P are taken from the upper entries of the
+ * neighbour (AW(P) = AE(W), AS(P) = AN(S), AB(P) = AT(B)).  Returns sum r^2. */
+double oracle_residual_sym(int nx, int ny, int nz,
+                           const double *ap, const double *ae, const double *an, const double *at,
+                           const double *b, const double *x, double *r) {
+  nsum acc = {0.0, 0.0};
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t p = ID(i, j, k);
+        double ax = ap[p] * x[p];
+        if (i + 1 < nx) ax += ae[p] * x[ID(i + 1, j, k)];
+        if (i > 0) { size_t w = ID(i - 1, j, k); ax += ae[w] * x[w]; }
+        if (j + 1 < ny) ax += an[p] * x[ID(i, j + 1, k)];
+        if (j > 0) { size_t s = ID(i, j - 1, k); ax += an[s] * x[s]; }
+        if (k + 1 < nz) ax += at[p] * x[ID(i, j, k + 1)];
+        if (k > 0) { size_t q = ID(i, j, k - 1); ax += at[q] * x[q]; }
+        double rp = b[p] - ax;
+        if (r) r[p] = rp;
+        nsum_add(&acc, rp * rp);
+      }
+  return nsum_get(&acc);
+}
+
+/* forward substitution L y = r (ascending lexicographic order) */
+void oracle_forward(int nx, int ny, int nz, const double *lb, const double *lw,
+                    const double *ls, const double *lp, const double *r, double *y) {
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t p = ID(i, j, k);
+        double v = r[p];
+        if (k > 0) v -= lb[p] * y[ID(i, j, k - 1)];
+        if (i > 0) v -= lw[p] * y[ID(i - 1, j, k)];
+        if (j > 0) v -= ls[p] * y[ID(i, j - 1, k)];
+        y[p] = v / lp[p];
+      }
+}
+
+/* backward substitution U d = y (descending lexicographic order) */
+void oracle_backward(int nx, int ny, int nz, const double *un, const double *ue,
+                     const double *ut, const double *y, double *d) {
+  for (int k = nz - 1; k >= 0; --k)
+    for (int j = ny - 1; j >= 0; --j)
+      for (int i = nx - 1; i >= 0; --i) {
+        size_t p = ID(i, j, k);
+        double v = y[p];
+        if (i + 1 < nx) v -= ue[p] * d[ID(i + 1, j, k)];
+        if (j + 1 < ny) v -= un[p] * d[ID(i, j + 1, k)];
+        if (k + 1 < nz) v -= ut[p] * d[ID(i, j, k + 1)];
+        d[p] = v;
+      }
+}
+
+/* One SIP iteration on x (in place).  r, y and d are work arrays of n
+ * doubles (residual, forward result, correction).  Returns ||b - A x_in||^2. */
+double oracle_iterate(int nx, int ny, int nz,
+                      const double *ap, const double *aw, const double *ae, const double *as,
+                      const double *an, const double *ab, const double *at,
+                      const double *lb, const double *lw, const double *ls, const double *lp,
+                      const double *un, const double *ue, const double *ut,
+                      const double *b, double *x, double *r, double *y, double *d) {
+  size_t n = (size_t)nx * ny * nz;
+  double rr = oracle_residual(nx, ny, nz, ap, aw, ae, as, an, ab, at, b, x, r);
+  oracle_forward(nx, ny, nz, lb, lw, ls, lp, r, y);
+  oracle_backward(nx, ny, nz, un, ue, ut, y, d);
+  for (size_t p = 0; p < n; ++p) x[p] += d[p];
+  return rr;
+}
+
+/* SIP to a relative residual.  Stop rule: with relres(x_n) computed from the
+ * residual of x_n, stop as soon as relres(x_n) <= rtol or n == max_iters;
+ * x_n is returned.  hist (nullable, max_iters+1 doubles) receives relres(x_0..x_n).
+ * Returns n (number of updates applied); *relres_out = relres(x_n). */
+int oracle_solve(int nx, int ny, int nz,
+                 const double *ap, const double *aw, const double *ae, const double *as,
+                 const double *an, const double *ab, const double *at,
+                 const double *lb, const double *lw, const double *ls, const double *lp,
+                 const double *un, const double *ue, const double *ut,
+                 const double *b, double *x, double rtol, int max_iters,
+                 double *hist, double *relres_out) {
+  size_t n = (size_t)nx * ny * nz;
+  double *r = (double *)malloc(n * sizeof(double));
+  double *y = (double *)malloc(n * sizeof(double));
+  double *d = (double *)malloc(n * sizeof(double));
+  double bb = sqrt(oracle_dot_sq((int64_t)n, b));
+  double scale = bb > 0.0 ? bb : 1.0;
+  int it = 0;
+  double rel = 0.0;
+  for (;;) {
+    double rr = oracle_residual(nx, ny, nz, ap, aw, ae, as, an, ab, at, b, x, r);
+    rel = sqrt(rr) / scale;
+    if (hist) hist[it] = rel;
+    if (rel <= rtol || it >= max_iters) break;
+    oracle_forward(nx, ny, nz, lb, lw, ls, lp, r, y);
+    oracle_backward(nx, ny, nz, un, ue, ut, y, d);
+    for (size_t p = 0; p < n; ++p) x[p] += d[p];
+    ++it;
+  }
+  free(r); free(y); free(d);
+  if (relres_out) *relres_out = rel;
+  return it;
+}
+
+/* ------------------------------------------------------------------ */
+/* Single precision.  The same steps in float arithmetic on float copies of
+ * A, of the factors (rounded from the FP64 factors) and of b and x.  This is
+ * the arithmetic of the paper's single-precision relaxation (Sec. 4.1: rhs and
+ * solution converted to single, relaxed in single, converted back). */
+#define IDF ID
+static void f32_residual(int nx, int ny, int nz, const float *ap, const float *aw,
+                         const float *ae, const float *as, const float *an, const float *ab,
+                         const float *at, const float *b, const float *x, float *r, int x_is_zero) {
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t p = IDF(i, j, k);
+        if (x_is_zero) { r[p] = b[p]; continue; }
+        float ax = ap[p] * x[p];
+        if (i > 0) ax += aw[p] * x[IDF(i - 1, j, k)];
+        if (i + 1 < nx) ax += ae[p] * x[IDF(i + 1, j, k)];
+        if (j > 0) ax += as[p] * x[IDF(i, j - 1, k)];
+        if (j + 1 < ny) ax += an[p] * x[IDF(i, j + 1, k)];
+        if (k > 0) ax += ab[p] * x[IDF(i, j, k - 1)];
+        if (k + 1 < nz) ax += at[p] * x[IDF(i, j, k + 1)];
+        r[p] = b[p] - ax;
+      }
+}
+static void f32_forward(int nx, int ny, int nz, const float *lb, const float *lw,
+                        const float *ls, const float *lp, const float *r, float *y) {
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t p = IDF(i, j, k);
+        float v = r[p];
+        if (k > 0) v -= lb[p] * y[IDF(i, j, k - 1)];
+        if (i > 0) v -= lw[p] * y[IDF(i - 1, j, k)];
+        if (j > 0) v -= ls[p] * y[IDF(i, j - 1, k)];
+        y[p] = v / lp[p];
+      }
+}
+static void f32_backward(int nx, int ny, int nz, const float *un, const float *ue,
+                         const float *ut, const float *y, float *d) {
+  for (int k = nz - 1; k >= 0; --k)
+    for (int j = ny - 1; j >= 0; --j)
+      for (int i = nx - 1; i >= 0; --i) {
+        size_t p = IDF(i, j, k);
+        float v = y[p];
+        if (i + 1 < nx) v -= ue[p] * d[IDF(i + 1, j, k)];
+        if (j + 1 < ny) v -= un[p] * d[IDF(i, j + 1, k)];
+        if (k + 1 < nz) v -= ut[p] * d[IDF(i, j, k + 1)];
+        d[p] = v;
+      }
+}
+
+/* One single-precision SIP iteration on x (in place); r, y, d: float work. */
+void oracle_iterate_f32(int nx, int ny, int nz,
+                        const float *ap, const float *aw, const float *ae, const float *as,
+                        const float *an, const float *ab, const float *at,
+                        const float *lb, const float *lw, const float *ls, const float *lp,
+                        const float *un, const float *ue, const float *ut,
+                        const float *b, float *x, int x_is_zero, float *r, float *y, float *d) {
+  size_t n = (size_t)nx * ny * nz;
+  f32_residual(nx, ny, nz, ap, aw, ae, as, an, ab, at, b, x, r, x_is_zero);
+  f32_forward(nx, ny, nz, lb, lw, ls, lp, r, y);
+  f32_backward(nx, ny, nz, un, ue, ut, y, d);
+  for (size_t p = 0; p < n; ++p) x[p] = (x_is_zero ? 0.0f : x[p]) + d[p];
+}
+
+/* ------------------------------------------------------------------ */
+/* Mixed precision: FP64 outer iterative refinement around single-precision
+ * SIP sweeps.  Outer step: r = b - A64 x in double, relres from it; stop as
+ * in oracle_solve; otherwise r32 = (float) r, m single-precision SIP
+ * iterations on A32 d = r32 starting from d = 0, then x += (double) d.
+ * Returns the number of outer corrections applied; hist (nullable,
+ * max_outer+1) receives the FP64 relres before each correction. */
+int oracle_solve_refined(int nx, int ny, int nz,
+                         const double *ap, const double *aw, const double *ae, const double *as,
+                         const double *an, const double *ab, const double *at,
+                         const float *ap32, const float *aw32, const float *ae32, const float *as32,
+                         const float *an32, const float *ab32, const float *at32,
+                         const float *lb32, const float *lw32, const float *ls32, const float *lp32,
+                         const float *un32, const float *ue32, const float *ut32,
+                         const double *b, double *x, double rtol, int max_outer, int m_inner,
+                         double *hist, double *relres_out) {
+  size_t n = (size_t)nx * ny * nz;
+  double *r = (double *)malloc(n * sizeof(double));
+  float *r32 = (float *)malloc(n * sizeof(float));
+  float *d32 = (float *)malloc(n * sizeof(float));
+  float *w1 = (float *)malloc(n * sizeof(float));
+  float *w2 = (float *)malloc(n * sizeof(float));
+  float *w3 = (float *)malloc(n * sizeof(float));
+  double bb = sqrt(oracle_dot_sq((int64_t)n, b));
+  double scale = bb > 0.0 ? bb : 1.0;
+  int it = 0;
+  double rel = 0.0;
+  for (;;) {
+    double rr = oracle_residual(nx, ny, nz, ap, aw, ae, as, an, ab, at, b, x, r);
+    rel = sqrt(rr) / scale;
+    if (hist) hist[it] = rel;
+    if (rel <= rtol || it >= max_outer) break;
+    for (size_t p = 0; p < n; ++p) r32[p] = (float)r[p];
+    for (int m = 0; m < m_inner; ++m)
+      oracle_iterate_f32(nx, ny, nz, ap32, aw32, ae32, as32, an32, ab32, at32, lb32, lw32, ls32,
+                         lp32, un32, ue32, ut32, r32, d32, m == 0, w1, w2, w3);
+    for (size_t p = 0; p < n; ++p) x[p] += (double)d32[p];
+    ++it;
+  }
+  free(r); free(r32); free(d32); free(w1); free(w2); free(w3);
+  if (relres_out) *relres_out = rel;
+  return it;
+}
