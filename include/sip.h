@@ -1,0 +1,165 @@
+/*
+ * sip.h -- C ABI of the GB300 (sm_103a) Stone SIP solver, libsip.so.
+ *
+ * The operation: Stone's strongly implicit procedure (SIP), the linear solver
+ * of the FASTEST-3D finite-volume code (Scheit, Hager, Treibig, Becker,
+ * Wellein, arXiv:1303.4538, Sec. 1; its factorisation lu3d, residual and
+ * forward substitution resforward3d and backward substitution backward3d are
+ * the routines of Tables 1-4), for the 7-point system A x = b of each
+ * hexahedral block:
+ *
+ *   factorisation  L U = A + N   (Stone's alpha-weighted auxiliary matrix N)
+ *   iteration      r = b - A x;  L y = r (ascending);  U d = y (descending);
+ *                  x <- x + d;   relres = ||r||_2 / ||b||_2
+ *
+ * Following the paper's solver redesign (Sec. 4.1: the solver owns its
+ * coefficient copies, the factorisation is computed once before the
+ * relaxation and reused), sip_factor builds a plan that owns reordered copies
+ * of A and the factors; sip_iterate / sip_solve relax with them.
+ *
+ * Conventions
+ *   - Cell (i,j,k), 0-based; natural layout p = i + nx*(j + ny*k) (i fastest).
+ *   - Lower neighbours W=(i-1,j,k), S=(i,j-1,k), B=(i,j,k-1); upper E, N, T.
+ *   - A holds matrix entries (diagonal AP, off-diagonals AW..AT, normally <= 0;
+ *     the paper's Listing 1 stores a_nb = -A_nb).  A coefficient that points
+ *     outside its block is ignored (treated as 0), except on a declared
+ *     interface (sip_interface), where it couples to the neighbour block.
+ *   - All array pointers are DEVICE pointers on the context's device unless
+ *     stated otherwise.  Host pointers are marked "host".
+ *   - All work is ordered on the context's stream.  Functions that return host
+ *     values synchronise that stream before returning.
+ *   - There is no CPU fallback: without a usable CUDA device every call that
+ *     needs one returns SIP_ERR_NO_DEVICE.
+ *
+ * Return codes: SIP_OK (0), SIP_NOT_CONVERGED (1, outputs valid), or a
+ * negative error.  After an error, sip_last_error(ctx) describes it.
+ * A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef SIP_H
+#define SIP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SIP_OK 0
+#define SIP_NOT_CONVERGED 1
+#define SIP_ERR_INVALID_ARG (-1)
+#define SIP_ERR_NO_DEVICE (-2)
+#define SIP_ERR_CUDA (-3)
+#define SIP_ERR_OOM (-4)
+#define SIP_ERR_BREAKDOWN (-5)      /* zero/non-finite pivot or denominator in the factorisation */
+#define SIP_ERR_DEVICE_TIMEOUT (-6) /* a bounded device-side wait gave up (no hang) */
+#define SIP_ERR_BUSY (-7)           /* server queue full */
+#define SIP_ERR_NOT_FOUND (-8)      /* unknown ticket */
+
+typedef struct sip_ctx sip_ctx;
+typedef struct sip_plan sip_plan;
+
+/* Arithmetic of the relaxation sweeps. */
+typedef enum {
+  SIP_MODE_F64 = 0,         /* FP64 sweeps, FP64 factors */
+  SIP_MODE_F32_REFINED = 1, /* FP32 sweeps inside an FP64 residual / refinement loop */
+  SIP_MODE_F32 = 2          /* FP32 sweeps only (the paper's single-precision relaxation) */
+} sip_mode;
+
+/* One block's system.  Lifetimes: the coefficient arrays are read during
+ * sip_factor only (the plan keeps reordered copies).  b and x must stay
+ * valid, and b unmodified, during every sip_iterate / sip_solve call on the
+ * plan; x is read as the initial guess and overwritten with the result. */
+typedef struct {
+  int32_t nx, ny, nz;      /* >= 1 each; nx*ny*nz < 2^31 */
+  int32_t coef_dtype;      /* 0: coefficient arrays are double, 1: float */
+  const void *ap, *aw, *ae, *as, *an, *ab, *at; /* device, natural layout, N entries each.
+                              If symmetric != 0, aw/as/ab may be NULL: then
+                              AW(P) = AE(W), AS(P) = AN(S), AB(P) = AT(B). */
+  const double *b;         /* device, natural layout, N doubles */
+  double *x;               /* device, natural layout, N doubles */
+  int32_t symmetric;       /* 1: A is symmetric (pressure-correction systems, Sec. 4.1) */
+} sip_block_desc;
+
+/* Interface between two blocks of a multi-block mesh (block-structured mesh,
+ * Sec. 1; exchange at block boundaries, Sec. 4.2): the +x face of blk_lo touches
+ * the -x face of blk_hi on the rectangle j < nj, k < nk (both anchored at
+ * j = k = 0).  Across it, blk_lo's AE at i = nx-1 and blk_hi's AW at i = 0
+ * couple the two blocks; the coupling enters each block's residual with the
+ * neighbour's values from the previous iteration (lagged, block Jacobi). */
+typedef struct {
+  int32_t blk_lo, blk_hi;
+  int32_t nj, nk;
+} sip_interface;
+
+typedef struct {
+  double alpha;            /* Stone's cancellation parameter, 0 <= alpha <= 1 (e.g. 0.92) */
+  int32_t mode;            /* sip_mode */
+  int32_t inner_iters;     /* SIP_MODE_F32_REFINED: FP32 iterations per FP64 correction (>= 1) */
+  int64_t max_spin;        /* polls before a device wait gives up (<= 0: default 2^22) */
+  int32_t tile_j, tile_k;  /* column-tile shape of the sweeps (0: chosen by the autotuner) */
+  int32_t check_every;     /* reserved, must be 0 or 1 */
+  int32_t debug_stall;     /* test hook: 1 makes the sweeps wait for a tag no producer
+                              writes, so the bounded waits time out (SIP_ERR_DEVICE_TIMEOUT) */
+} sip_options;
+
+/* Fills *opt with defaults: alpha 0.92, SIP_MODE_F64, inner_iters 4. Host pointer. */
+void sip_default_options(sip_options *opt);
+
+/* Creates a context on CUDA device `device`, ordering all work on `stream`
+ * (a cudaStream_t; NULL = legacy default stream).  *ctx (host) receives the
+ * handle.  Errors: SIP_ERR_NO_DEVICE, SIP_ERR_INVALID_ARG. */
+int sip_create(sip_ctx **ctx, int device, void *stream);
+int sip_destroy(sip_ctx *ctx);
+/* Description of the last error on ctx (never NULL; valid until the next
+ * call on this thread).  ctx == NULL: the last sip_create failure. */
+const char *sip_last_error(sip_ctx *ctx);
+
+/* Validates the blocks, copies their coefficients into the plan's plane
+ * layout, computes Stone's factorisation (lu3d, Sec. 4.1: once, kept for
+ * all later relaxations) and returns the plan in *plan (host).  The plan owns
+ * all device memory it allocates.  nifaces > 0 couples blocks (batched mesh).
+ * Errors: SIP_ERR_INVALID_ARG, SIP_ERR_OOM, SIP_ERR_CUDA, SIP_ERR_BREAKDOWN,
+ * SIP_ERR_DEVICE_TIMEOUT. */
+int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks,
+               const sip_interface *ifaces, int nifaces, const sip_options *opt,
+               sip_plan **plan);
+
+/* Runs exactly `niters` SIP iterations on every block's x (resforward3d then
+ * backward3d per iteration, Tables 1-4).  relres_out (host, nullable) receives
+ * relres of x before the last update (the norm computed by the last
+ * iteration's residual).  In SIP_MODE_F32_REFINED an "iteration" is one FP64
+ * correction of inner_iters FP32 iterations.  Errors as above. */
+int sip_iterate(sip_plan *plan, int niters, double *relres_out);
+
+/* Iterates until relres(x_n) <= rtol or n == max_iters, where relres(x_n) is
+ * computed from the residual of x_n and x_n is returned (the forward result
+ * of the deciding iteration is discarded).  iters_out (host, nullable) = n,
+ * the number of updates applied (FP64 corrections in the refined mode);
+ * relres_out (host, nullable) = relres(x_n).  Returns SIP_OK or
+ * SIP_NOT_CONVERGED. */
+int sip_solve(sip_plan *plan, double rtol, int max_iters, int *iters_out, double *relres_out);
+
+/* Copies the relres history of the last sip_iterate/sip_solve call into
+ * host_out (host, up to cap doubles); *n_out (host) = entries available. */
+int sip_get_history(sip_plan *plan, double *host_out, int cap, int *n_out);
+
+/* Writes block `blk`'s FP64 factors in natural layout into seven device
+ * arrays of N doubles: LB, LW, LS, 1/LP, UN, UE, UT (test and inspection aid). */
+int sip_export_factors(sip_plan *plan, int blk, double *const out[7]);
+
+/* Plane layout used by the sweeps (host-only helper, no device needed):
+ * fills rbT (host, nz * (nx+ny+nz-2) int32) so that cell (i,j,k) is stored at
+ * rbT[k*(nx+ny+nz-2) + i+j+k] + j of its block's plan arrays.  Cells of one
+ * hyperplane i+j+k = s are contiguous, rows k ascend within a plane and j
+ * ascends within a row.  Entries of empty rows are INT32_MIN. */
+int sip_plane_layout(int nx, int ny, int nz, int32_t *rbT);
+
+/* Total device bytes owned by the plan (host out). */
+int sip_plan_bytes(sip_plan *plan, size_t *bytes_out);
+int sip_plan_destroy(sip_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIP_H */

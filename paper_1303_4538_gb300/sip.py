@@ -1,0 +1,233 @@
+"""Python binding of libsip.so (include/sip.h): argument marshalling only.
+
+Every step of the solver runs in the library's sm_103a kernels; this module
+passes device pointers of torch CUDA tensors and host scalars through ctypes.
+There is no fallback: if the library cannot be loaded, or no CUDA device is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsip.so")
+
+SIP_OK = 0
+SIP_NOT_CONVERGED = 1
+SIP_ERR_INVALID_ARG = -1
+SIP_ERR_NO_DEVICE = -2
+SIP_ERR_CUDA = -3
+SIP_ERR_OOM = -4
+SIP_ERR_BREAKDOWN = -5
+SIP_ERR_DEVICE_TIMEOUT = -6
+SIP_ERR_BUSY = -7
+SIP_ERR_NOT_FOUND = -8
+
+SIP_MODE_F64 = 0
+SIP_MODE_F32_REFINED = 1
+SIP_MODE_F32 = 2
+
+ERROR_NAMES = {
+    SIP_ERR_INVALID_ARG: "SIP_ERR_INVALID_ARG", SIP_ERR_NO_DEVICE: "SIP_ERR_NO_DEVICE",
+    SIP_ERR_CUDA: "SIP_ERR_CUDA", SIP_ERR_OOM: "SIP_ERR_OOM", SIP_ERR_BREAKDOWN: "SIP_ERR_BREAKDOWN",
+    SIP_ERR_DEVICE_TIMEOUT: "SIP_ERR_DEVICE_TIMEOUT", SIP_ERR_BUSY: "SIP_ERR_BUSY",
+    SIP_ERR_NOT_FOUND: "SIP_ERR_NOT_FOUND",
+}
+
+# every symbol include/sip.h declares
+EXPORTED = (
+    "sip_default_options", "sip_create", "sip_destroy", "sip_last_error", "sip_factor",
+    "sip_iterate", "sip_solve", "sip_get_history", "sip_export_factors", "sip_plan_bytes",
+    "sip_plan_destroy", "sip_plane_layout",
+)
+
+
+class sip_block_desc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("coef_dtype", ctypes.c_int32),
+        ("ap", ctypes.c_void_p), ("aw", ctypes.c_void_p), ("ae", ctypes.c_void_p),
+        ("as_", ctypes.c_void_p), ("an", ctypes.c_void_p), ("ab", ctypes.c_void_p),
+        ("at", ctypes.c_void_p),
+        ("b", ctypes.c_void_p), ("x", ctypes.c_void_p),
+        ("symmetric", ctypes.c_int32),
+    ]
+
+
+class sip_interface(ctypes.Structure):
+    _fields_ = [("blk_lo", ctypes.c_int32), ("blk_hi", ctypes.c_int32),
+                ("nj", ctypes.c_int32), ("nk", ctypes.c_int32)]
+
+
+class sip_options(ctypes.Structure):
+    _fields_ = [
+        ("alpha", ctypes.c_double), ("mode", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
+        ("max_spin", ctypes.c_int64), ("tile_j", ctypes.c_int32), ("tile_k", ctypes.c_int32),
+        ("check_every", ctypes.c_int32), ("debug_stall", ctypes.c_int32),
+    ]
+
+
+class SipError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libsip.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} not built; run paper_1303_4538_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        D = ctypes.c_double
+        L.sip_default_options.argtypes = [ctypes.POINTER(sip_options)]
+        L.sip_default_options.restype = None
+        L.sip_create.argtypes = [ctypes.POINTER(P), I, P]
+        L.sip_destroy.argtypes = [P]
+        L.sip_last_error.argtypes = [P]
+        L.sip_last_error.restype = ctypes.c_char_p
+        L.sip_factor.argtypes = [P, ctypes.POINTER(sip_block_desc), I, ctypes.POINTER(sip_interface), I,
+                                 ctypes.POINTER(sip_options), ctypes.POINTER(P)]
+        L.sip_iterate.argtypes = [P, I, ctypes.POINTER(D)]
+        L.sip_solve.argtypes = [P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
+        L.sip_get_history.argtypes = [P, ctypes.POINTER(D), I, ctypes.POINTER(I)]
+        L.sip_export_factors.argtypes = [P, I, ctypes.POINTER(P)]
+        L.sip_plan_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        L.sip_plan_destroy.argtypes = [P]
+        L.sip_plane_layout.argtypes = [I, I, I, P]
+        for name in EXPORTED:
+            if name not in ("sip_default_options", "sip_last_error"):
+                getattr(L, name).restype = I
+        _lib = L
+    return _lib
+
+
+def default_options(**kw) -> sip_options:
+    o = sip_options()
+    lib().sip_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return int(t.data_ptr())
+
+
+class Context:
+    """sip_create / sip_destroy around a device and a CUDA stream handle."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        self.h = ctypes.c_void_p()
+        rc = lib().sip_create(ctypes.byref(self.h), int(device), ctypes.c_void_p(stream or 0))
+        if rc != SIP_OK:
+            raise SipError(rc, "sip_create failed: " + lib().sip_last_error(None).decode())
+
+    def check(self, rc: int, allow_not_converged: bool = False) -> int:
+        if rc == SIP_OK or (allow_not_converged and rc == SIP_NOT_CONVERGED):
+            return rc
+        raise SipError(rc, lib().sip_last_error(self.h).decode())
+
+    def close(self):
+        if self.h:
+            lib().sip_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_desc(nx, ny, nz, coefs: Sequence, b, x, symmetric: bool = False,
+              coef_dtype: int = 0) -> sip_block_desc:
+    """coefs: (ap, aw, ae, as, an, ab, at) device tensors or pointers (aw/as/ab
+    may be None when symmetric); b, x: FP64 device tensors (natural layout)."""
+    d = sip_block_desc()
+    d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
+    d.coef_dtype = int(coef_dtype)
+    d.ap, d.aw, d.ae, d.as_, d.an, d.ab, d.at = [_ptr(c) for c in coefs]
+    d.b = _ptr(b)
+    d.x = _ptr(x)
+    d.symmetric = 1 if symmetric else 0
+    return d
+
+
+class Plan:
+    """sip_factor / sip_iterate / sip_solve / sip_plan_destroy."""
+
+    def __init__(self, ctx: Context, descs: List[sip_block_desc], opts: Optional[sip_options] = None,
+                 ifaces: Optional[List[sip_interface]] = None, keep=None):
+        self.ctx = ctx
+        self.h = ctypes.c_void_p()
+        self._keep = keep  # tensors that must outlive the plan (b, x, ...)
+        arr = (sip_block_desc * len(descs))(*descs)
+        nif = len(ifaces) if ifaces else 0
+        iarr = (sip_interface * nif)(*ifaces) if nif else None
+        rc = lib().sip_factor(ctx.h, arr, len(descs), iarr, nif,
+                              ctypes.byref(opts) if opts is not None else None, ctypes.byref(self.h))
+        ctx.check(rc)
+
+    def iterate(self, niters: int) -> float:
+        rel = ctypes.c_double(0.0)
+        self.ctx.check(lib().sip_iterate(self.h, int(niters), ctypes.byref(rel)))
+        return rel.value
+
+    def solve(self, rtol: float, max_iters: int):
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        rc = lib().sip_solve(self.h, float(rtol), int(max_iters), ctypes.byref(it), ctypes.byref(rel))
+        self.ctx.check(rc, allow_not_converged=True)
+        return it.value, rel.value, rc == SIP_OK
+
+    def history(self) -> List[float]:
+        n = ctypes.c_int(0)
+        self.ctx.check(lib().sip_get_history(self.h, None, 0, ctypes.byref(n)))
+        buf = (ctypes.c_double * max(n.value, 1))()
+        self.ctx.check(lib().sip_get_history(self.h, buf, n.value, ctypes.byref(n)))
+        return list(buf[: n.value])
+
+    def export_factors(self, blk: int, outs) -> None:
+        arr = (ctypes.c_void_p * 7)(*[_ptr(o) for o in outs])
+        self.ctx.check(lib().sip_export_factors(self.h, int(blk), arr))
+
+    def nbytes(self) -> int:
+        b = ctypes.c_size_t(0)
+        self.ctx.check(lib().sip_plan_bytes(self.h, ctypes.byref(b)))
+        return b.value
+
+    def close(self):
+        if self.h:
+            lib().sip_plan_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plane_layout(nx: int, ny: int, nz: int):
+    """Host-side plane layout table (no GPU needed): int32 array of shape
+    (nz, nx+ny+nz-2); cell (i, j, k) sits at table[k, i+j+k] + j."""
+    import numpy as np
+    npl = nx + ny + nz - 2
+    out = np.zeros((nz, npl), dtype=np.int32)
+    rc = lib().sip_plane_layout(int(nx), int(ny), int(nz), out.ctypes.data_as(ctypes.c_void_p))
+    if rc != SIP_OK:
+        raise SipError(rc, "sip_plane_layout failed")
+    return out
