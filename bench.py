@@ -1,0 +1,413 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 SIP solver (libsip.so through its C ABI).
+
+Workload: the 256^3 pressure-Poisson block (16.8 M cells, symmetric 7-point
+matrix with one Dirichlet face, alpha = 0.92), seeded synthetic inputs.
+
+A step is one sip_solve call on the factored plan: the right-hand side and
+the initial guess are copied into the plane layout, SIP iterations run with
+the device-side stop rule (rtol 1e-8, at most --iters iterations per step),
+and x is copied back; x is reset to 0 before every step.  `value` is the
+FP32-refined solver's SIP rate in MLUP/s (cells x FP32 SIP iterations / step
+time, the FP64 residual/refinement passes included in the time); the plain
+FP64 solver is measured the same way under "fp64".  The factorisation is
+timed separately (factor_ms).
+
+--impl reference times the CPU oracle (plain C, one thread) on a bounded
+sample of the same workload: each step is one FP64 SIP iteration of the
+256^3 block.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SIP MLUP/s & %HBM roofline, FP32-refined vs FP64; p50/p99 solve latency"
+
+# Algorithmic bytes per cell per launch of each kernel kind (each array read or
+# written once; neighbour values reused on chip).  Words of 8 B (FP64) or 4 B.
+ALGO_BYTES = {
+    "factor": 7 * 8 + 7 * 8,           # A in, LB LW LS 1/LP UN UE UT out
+    "fwd64": 14 * 8,                   # A(7) b x LB LW LS 1/LP in, y out
+    "fwd64_sym": 11 * 8,               # AP AE AN AT b x LB LW LS 1/LP in, y out
+    "bwd64": 6 * 8,                    # UE UN UT y x in, x out
+    "fwd32": 14 * 4, "fwd32_norm": 14 * 4,
+    "fwd32_sym": 11 * 4, "fwd32_sym_norm": 11 * 4,
+    "fwd32_x0": 6 * 4,                 # LB LW LS 1/LP r in, y out
+    "bwd32": 6 * 4,                    # UE UN UT y d in, d out
+    "bwd32_x0": 5 * 4,                 # UE UN UT y in, d out
+    "bwd32_upd64": 5 * 4 + 16,         # UE UN UT y d in, x64 in/out
+    "bwd32_x0_upd64": 4 * 4 + 16,      # UE UN UT y in, x64 in/out
+    "resid64": 7 * 8 + 16 + 4,         # A(7) b x in, r32 out
+    "resid64_sym": 4 * 8 + 16 + 4,
+    "resid64_a32": 7 * 4 + 16 + 4,
+    "resid64_a32_sym": 4 * 4 + 16 + 4,
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="cube edge of the Poisson block")
+    ap.add_argument("--iters", type=int, default=100,
+                    help="max FP64 corrections (refined) / iterations (fp64) per step")
+    ap.add_argument("--inner", type=int, default=4, help="FP32 iterations per FP64 correction")
+    ap.add_argument("--ttol", action="store_true", help="also time full solves to 1e-8")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=3)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.proc:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[2][q].lower().startswith("active")})
+        out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(r[1] for r in rows), reasons=reasons,
+                   samples=len(rows))
+        return out
+
+
+def src_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1303_4538_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("src_hash") != src_hash():
+        return None
+    v = d.get("kernels", {}).get(kernel)
+    return v.get("bytes_per_launch_full") if isinstance(v, dict) else None
+
+
+def peaks():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ oracle
+def cpu_baseline(blk, iters: int):
+    import numpy as np
+    import oracle
+    n = blk.nx
+    F = oracle.factor(n, n, n, blk.coefs, 0.92)
+    x = np.zeros(blk.n)
+    oracle.iterate(n, n, n, blk.coefs, F, blk.b, x)  # warm
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        oracle.iterate(n, n, n, blk.coefs, F, blk.b, x)
+    dt = time.perf_counter() - t0
+    return blk.n * iters / dt / 1e6, dt
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.destroy_process_group()
+            return
+    import numpy as np
+    import oracle
+    from paper_1303_4538_gb300 import workloads as W
+    blk = W.poisson_256cube(args.n)
+    n = blk.nx
+    F = oracle.factor(n, n, n, blk.coefs, 0.92)
+    x = np.zeros(blk.n)
+    for _ in range(args.warmup):
+        oracle.iterate(n, n, n, blk.coefs, F, blk.b, x)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.iterate(n, n, n, blk.coefs, F, blk.b, x)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = blk.n * args.steps / tot / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"poisson_{n}cube", "cells": blk.n, "alpha": 0.92,
+                   "step": "one FP64 SIP iteration (residual, forward, backward, update, norm)"},
+        "cpu_baseline": {"value": value, "unit": "MLUP/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} FP64 SIP iterations of the {n}^3 Poisson block, 1 thread"},
+        "e2e": {"value": value, "unit": "MLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ GPU path
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    from paper_1303_4538_gb300 import build as B
+    from paper_1303_4538_gb300 import sip
+    from paper_1303_4538_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    sip.lib()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    blk = W.poisson_256cube(args.n)
+    N = blk.n
+    stream = torch.cuda.current_stream()
+    ctx = sip.Context(local, stream.cuda_stream)
+    A = [torch.from_numpy(c).cuda() for c in blk.coef_list()]
+    b = torch.from_numpy(blk.b).cuda()
+    x = torch.zeros(N, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    desc = sip.make_desc(blk.nx, blk.ny, blk.nz, [A[0], None, A[2], None, A[4], None, A[6]], b, x, symmetric=True)
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan_r = sip.Plan(ctx, [desc], sip.default_options(mode=sip.SIP_MODE_F32_REFINED, inner_iters=args.inner))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    factor_ms_r = e0.elapsed_time(e1)
+    e0.record(stream)
+    plan_d = sip.Plan(ctx, [desc], sip.default_options(mode=sip.SIP_MODE_F64))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    factor_ms_d = e0.elapsed_time(e1)
+    del A
+    torch.cuda.empty_cache()
+
+    def step(plan):
+        x.zero_()
+        return plan.solve(1e-8, args.iters)
+
+    def timed(plan, inner, K, prof=False):
+        barrier()
+        if prof:
+            plan.profile(True)
+            plan.profile_read(reset=True)
+        l0 = plan.launches()
+        e0.record(stream)
+        its = 0
+        for _ in range(K):
+            it, rel, conv = step(plan)
+            its += it
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        prof_d = plan.profile_read(reset=True) if prof else {}
+        if prof:
+            plan.profile(False)
+        return ms, its * inner, plan.launches() - l0, prof_d
+
+    for _ in range(args.warmup):
+        step(plan_r)
+        step(plan_d)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_r, lup_iters_r, launches_r, prof_r = timed(plan_r, args.inner, args.steps, prof=True)
+    ms_d, lup_iters_d, launches_d, prof_d = timed(plan_d, 1, args.steps, prof=True)
+    clk = clocks.stop()
+
+    # end-to-end through the public API with host buffers
+    b_h = torch.from_numpy(blk.b).pin_memory()
+    x0_h = torch.zeros(N, dtype=torch.float64).pin_memory()
+    x_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    barrier()
+    e0.record(stream)
+    e2e_iters = 0
+    for _ in range(args.steps):
+        b.copy_(b_h, non_blocking=True)
+        x.copy_(x0_h, non_blocking=True)
+        it, rel, conv = plan_r.solve(1e-8, args.iters)
+        e2e_iters += it * args.inner
+        x_h.copy_(x, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+
+    ttol = {}
+    if args.ttol:
+        for name, plan, inner in (("f32_refined", plan_r, args.inner), ("f64", plan_d, 1)):
+            barrier()
+            x.zero_()
+            e0.record(stream)
+            it, rel, conv = plan.solve(1e-8, 1_000_000)
+            e1.record(stream)
+            barrier()
+            ttol[name] = {"seconds": e0.elapsed_time(e1) / 1e3, "iterations": it, "sip_iterations": it * inner,
+                          "relres": rel, "converged": conv}
+
+    def rates(ms, iters):
+        return N * iters / (ms / 1e3) / 1e6
+
+    val_r = rates(ms_r, lup_iters_r)
+    val_d = rates(ms_d, lup_iters_d)
+    val_e2e = rates(ms_e2e, e2e_iters)
+    if dist:
+        t = torch.tensor([ms_r, ms_d, ms_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        c = torch.tensor([lup_iters_r, lup_iters_d, e2e_iters], dtype=torch.float64, device="cuda")
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        ms_r, ms_d, ms_e2e = t.tolist()
+        val_r = N * c[0].item() / (ms_r / 1e3) / 1e6
+        val_d = N * c[1].item() / (ms_d / 1e3) / 1e6
+        val_e2e = N * c[2].item() / (ms_e2e / 1e3) / 1e6
+
+    hbm, src = peaks()
+
+    def roofline(prof):
+        sweep = {k: v for k, v in prof.items() if k in ALGO_BYTES}
+        if not sweep:
+            return None
+        k = max(sweep, key=lambda q: sweep[q][0])
+        tot_ms, n = sweep[k]
+        per_launch_s = tot_ms / n / 1e3
+        ach = ALGO_BYTES[k] * N / per_launch_s / 1e9
+        return {"bound": "hbm", "kernel": k, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "traffic": load_traffic(k), "peak_source": src,
+                "algo_bytes_per_cell": ALGO_BYTES[k], "cells_per_launch": N,
+                "avg_launch_us": round(per_launch_s * 1e6, 2),
+                "share": round(tot_ms / sum(v[0] for v in prof.values()), 4)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, dt = cpu_baseline(blk, args.cpu_iters)
+        cpu = {"value": v, "unit": "MLUP/s", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_iters} FP64 SIP iterations of the {args.n}^3 Poisson block "
+                         f"({dt:.1f} s, plain C, 1 thread)"}
+    line = {
+        "metric": METRIC, "value": round(val_r, 1), "unit": "MLUP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_r / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"poisson_{args.n}cube", "cells": N, "alpha": 0.92, "mode": "f32_refined",
+                   "inner_iters": args.inner, "max_corrections_per_step": args.iters, "rtol": 1e-8,
+                   "parallelism": f"replicas x{world}", "l2": "working set > L2 (plan arrays "
+                   f"{plan_r.nbytes() / 1e9:.2f} GB)", "step": "sip_solve on the factored plan, x reset to 0"},
+        "roofline": roofline(prof_r),
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(val_e2e, 1), "unit": "MLUP/s", "h2d_bytes_per_step": 2 * N * 8,
+                "d2h_bytes_per_step": N * 8},
+        "gpu_launches": int(launches_r),
+        "clocks": clk,
+        "fp64": {"value": round(val_d, 1), "unit": "MLUP/s", "ms_per_step": round(ms_d / args.steps, 3),
+                 "gpu_launches": int(launches_d), "roofline": roofline(prof_d)},
+        "factor_ms": {"f32_refined": round(factor_ms_r, 2), "f64": round(factor_ms_d, 2)},
+        "kernel_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in prof_r.items()},
+        "kernel_ms_fp64": {k: round(v[0] / max(v[1], 1), 4) for k, v in prof_d.items()},
+    }
+    if ttol:
+        line["time_to_1e-8"] = ttol
+    print(json.dumps(line), flush=True)
+    plan_r.close()
+    plan_d.close()
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

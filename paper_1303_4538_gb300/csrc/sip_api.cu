@@ -73,7 +73,9 @@ struct sip_plan {
   std::vector<sip_interface> ifaces;
   long long ncells = 0;
   int ntiles = 0;
-  int NT = 256, EC = 0, R64 = 6, R32 = 6;
+  int NT = 256, EC = 0, FS = 0;
+  int Rk[K_NKINDS] = {};     // stage depth chosen per kernel kind
+  int gridk[K_NKINDS] = {};  // resident CTAs per kernel kind (grid of the ticketed sweeps)
   std::vector<void *> allocs;
   size_t bytes = 0;
   DevBlock *d_blocks = nullptr;
@@ -96,8 +98,15 @@ struct sip_plan {
   int *tickets = nullptr;
   Ctl *h_ctl = nullptr;     // pinned [3]: two chunk snapshots, one final
   int *h_status = nullptr;  // pinned [2]
-  int grid_t = 1;        // CTAs of the ticketed sweeps
   int last_nhist = 0;
+  long long launches = 0;  // kernels launched by this plan
+  // kernel timing (sip_profile_*): event pairs per launch, read back lazily
+  bool prof = false;
+  struct Rec { int kind; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[K_NKINDS + 1] = {};
+  long long prof_n[K_NKINDS + 1] = {};
 };
 
 // ------------------------------------------------------------------ helpers
@@ -116,6 +125,13 @@ cudaError_t palloc(sip_plan *p, T **ptr, size_t count) {
 }
 
 void free_plan_memory(sip_plan *p) {
+  for (auto &r : p->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  p->recs.clear();
+  for (auto e : p->pool) cudaEventDestroy(e);
+  p->pool.clear();
   for (void *v : p->allocs) cudaFree(v);
   p->allocs.clear();
   if (p->h_ctl) cudaFreeHost(p->h_ctl);
@@ -226,6 +242,7 @@ SweepCommon common(sip_plan *p, bool backward, int ticket, int reset, int slot) 
   c.tiles = backward ? p->d_tiles_b : p->d_tiles_f;
   c.ntiles = p->ntiles;
   c.exch_cells = p->EC;
+  c.face_slots = p->FS;
   c.ticket = p->tickets + ticket;
   c.reset_ticket = reset >= 0 ? p->tickets + reset : nullptr;
   c.ctl = p->ctl;
@@ -237,15 +254,54 @@ SweepCommon common(sip_plan *p, bool backward, int ticket, int reset, int slot) 
   return c;
 }
 
+cudaEvent_t take_event(sip_plan *p) {
+  if (!p->pool.empty()) {
+    cudaEvent_t e = p->pool.back();
+    p->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Event pair around a launch when profiling; kind K_NKINDS = utility kernels.
+struct ProfScope {
+  sip_plan *p;
+  int kind;
+  cudaEvent_t a = nullptr;
+  ProfScope(sip_plan *p_, int k) : p(p_), kind(k) {
+    ++p->launches;
+    if (p->prof) {
+      a = take_event(p);
+      cudaEventRecord(a, p->ctx->stream);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = take_event(p);
+      cudaEventRecord(b, p->ctx->stream);
+      p->recs.push_back({kind, a, b});
+    }
+  }
+};
+
 template <typename Params>
-cudaError_t launch(sip_plan *p, int kind, int R, const Params &prm, bool ticketed) {
-  const size_t smem = kernel_smem(kind, R, p->NT, p->EC);
-  int grid = p->ntiles;
-  if (ticketed) grid = std::min(grid, p->grid_t);
-  else grid = std::min(grid, std::max(1, p->ctx->nsm * std::max(1, max_active(p, kind, R, smem))));
+cudaError_t launch(sip_plan *p, int kind, const Params &prm) {
+  const int R = p->Rk[kind];
+  const size_t smem = kernel_smem(kind, R, p->NT, p->EC, p->FS);
+  const int grid = std::max(1, std::min(p->ntiles, p->gridk[kind]));
   void *args[] = {(void *)&prm};
+  ProfScope ps(p, kind);
   return cudaLaunchKernel(kernel_ptr(kind, R), dim3(grid), dim3(p->NT), args, smem, p->ctx->stream);
 }
+
+// utility launches (layout, reductions, control) are counted as kind K_NKINDS
+#define UTIL(call) \
+  do {             \
+    ProfScope ps_(p, K_NKINDS); \
+    CU(call);      \
+  } while (0)
 
 int check_status(sip_plan *p) {
   sip_ctx *ctx = p->ctx;
@@ -269,13 +325,13 @@ int enqueue_iter_f64(sip_plan *p) {
   f.an = p->A64[4]; f.ab = p->A64[5]; f.at = p->A64[6];
   f.lb = p->F64[0]; f.lw = p->F64[1]; f.ls = p->F64[2]; f.rlp = p->F64[3];
   f.b = p->b64; f.x = p->x64; f.y = p->y64; f.partials = p->partials;
-  CU(launch(p, p->sym ? K_FWD64S : K_FWD64, p->R64, f, true));
-  CU(launch_finalize(p->partials, p->ntiles, p->ctl, p->hist, p->hist_cap, p->status, FIN_RELRES, ctx->stream));
+  CU(launch(p, p->sym ? K_FWD64S : K_FWD64, f));
+  UTIL(launch_finalize(p->partials, p->ntiles, p->ctl, p->hist, p->hist_cap, p->status, FIN_RELRES, ctx->stream));
   BwdParams<double> b;
   b.c = common(p, true, 1, 0, 1);
   b.ue = p->F64[5]; b.un = p->F64[4]; b.ut = p->F64[6];
   b.y = p->y64; b.x = p->x64; b.x64 = nullptr;
-  CU(launch(p, K_BWD64, p->R64, b, true));
+  CU(launch(p, K_BWD64, b));
   return SIP_OK;
 }
 
@@ -292,7 +348,7 @@ int enqueue_iter_refined(sip_plan *p) {
     r.ap = p->A32[0]; r.aw = p->A32[1]; r.ae = p->A32[2]; r.as = p->A32[3];
     r.an = p->A32[4]; r.ab = p->A32[5]; r.at = p->A32[6];
     r.b = p->b64; r.x = p->x64; r.r32 = p->r32; r.partials = p->partials;
-    CU(launch(p, p->sym ? K_RES32AS : K_RES32A, p->R64, r, false));
+    CU(launch(p, p->sym ? K_RES32AS : K_RES32A, r));
   } else {
     ResParams<double> r;
     r.blocks = p->d_blocks; r.tiles = p->d_tiles_f; r.ntiles = p->ntiles; r.exch_cells = p->EC;
@@ -300,9 +356,9 @@ int enqueue_iter_refined(sip_plan *p) {
     r.ap = p->A64[0]; r.aw = p->A64[1]; r.ae = p->A64[2]; r.as = p->A64[3];
     r.an = p->A64[4]; r.ab = p->A64[5]; r.at = p->A64[6];
     r.b = p->b64; r.x = p->x64; r.r32 = p->r32; r.partials = p->partials;
-    CU(launch(p, p->sym ? K_RES64S : K_RES64, p->R64, r, false));
+    CU(launch(p, p->sym ? K_RES64S : K_RES64, r));
   }
-  CU(launch_finalize(p->partials, p->ntiles, p->ctl, p->hist, p->hist_cap, p->status, FIN_RELRES, ctx->stream));
+  UTIL(launch_finalize(p->partials, p->ntiles, p->ctl, p->hist, p->hist_cap, p->status, FIN_RELRES, ctx->stream));
   for (int q = 0; q < m; ++q) {
     const bool first = q == 0, lastq = q == m - 1;
     FwdParams<float> f;
@@ -312,13 +368,13 @@ int enqueue_iter_refined(sip_plan *p) {
     f.lb = p->F32[0]; f.lw = p->F32[1]; f.ls = p->F32[2]; f.rlp = p->F32[3];
     f.b = p->r32; f.x = p->d32; f.y = p->y32; f.partials = nullptr;
     const int fk = first ? K_FWD32Z : (p->sym ? K_FWD32S : K_FWD32);
-    CU(launch(p, fk, p->R32, f, true));
+    CU(launch(p, fk, f));
     BwdParams<float> b;
     b.c = common(p, true, 1, 0, 1);
     b.ue = p->F32[5]; b.un = p->F32[4]; b.ut = p->F32[6];
     b.y = p->y32; b.x = p->d32; b.x64 = lastq ? p->x64 : nullptr;
     const int bk = first ? (lastq ? K_BWD32ZU : K_BWD32Z) : (lastq ? K_BWD32U : K_BWD32);
-    CU(launch(p, bk, p->R32, b, true));
+    CU(launch(p, bk, b));
   }
   return SIP_OK;
 }
@@ -331,19 +387,19 @@ int enqueue_iter(sip_plan *p) {
 int begin_sequence(sip_plan *p, double rtol, int max_iters) {
   sip_ctx *ctx = p->ctx;
   CU(cudaMemsetAsync(p->tickets, 0, 4 * sizeof(int), ctx->stream));
-  CU(launch_set_ctl(p->ctl, rtol, max_iters, ctx->stream));
+  UTIL(launch_set_ctl(p->ctl, rtol, max_iters, ctx->stream));
   for (auto &bh : p->blocks) {
-    CU(launch_to_plan_f64(bh.d.b, 0, p->b64, bh.db, 0, 0, ctx->stream));
-    CU(launch_to_plan_f64(bh.d.x, 0, p->x64, bh.db, 0, 0, ctx->stream));
+    UTIL(launch_to_plan_f64(bh.d.b, 0, p->b64, bh.db, 0, 0, ctx->stream));
+    UTIL(launch_to_plan_f64(bh.d.x, 0, p->x64, bh.db, 0, 0, ctx->stream));
   }
-  CU(launch_sumsq_partials(p->b64, p->ncells, p->bparts, p->nbparts, ctx->stream));
-  CU(launch_finalize(p->bparts, p->nbparts, p->ctl, p->hist, p->hist_cap, p->status, FIN_BNORM, ctx->stream));
+  UTIL(launch_sumsq_partials(p->b64, p->ncells, p->bparts, p->nbparts, ctx->stream));
+  UTIL(launch_finalize(p->bparts, p->nbparts, p->ctl, p->hist, p->hist_cap, p->status, FIN_BNORM, ctx->stream));
   return SIP_OK;
 }
 
 int end_sequence(sip_plan *p) {
   sip_ctx *ctx = p->ctx;
-  for (auto &bh : p->blocks) CU(launch_from_plan_f64(p->x64, bh.d.x, bh.db, ctx->stream));
+  for (auto &bh : p->blocks) UTIL(launch_from_plan_f64(p->x64, bh.d.x, bh.db, ctx->stream));
   CU(cudaMemcpyAsync(&p->h_ctl[2], p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
   int rc = check_status(p);  // synchronises
   if (rc != SIP_OK) return rc;
@@ -418,6 +474,7 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
   }
   p->NT = ts.TJ * ts.TK;
   p->EC = (ts.TJ + 2) * (ts.TK + 2);
+  p->FS = ts.TJ + ts.TK;
 
   // per-block layout tables and tile lists
   std::vector<DevBlock> hdb;
@@ -541,27 +598,27 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bail(e, "plan upload");
   }
-  // stage depth and resident grid of the ticketed sweeps
+  // Stage depth per kernel kind: the deepest ring (6, else 3) with which every
+  // tile of the plan is resident at once (one wave), else the one that keeps
+  // the most tiles resident.  The ticketed sweeps launch that many CTAs.
   {
-    auto fits = [&](int kind, int R) {
-      return kernel_smem(kind, R, p->NT, p->EC) + ctx->kernel_static_smem <= ctx->smem_optin;
-    };
-    const int k64 = sym ? K_FWD64S : K_FWD64;
-    p->R64 = fits(k64, 6) && fits(K_FACTOR, 6) ? 6 : 3;
-    p->R32 = fits(sym ? K_FWD32S : K_FWD32, 6) ? 6 : 3;
-    int occ = INT_MAX;
-    const int kinds64[] = {K_FACTOR, k64, K_BWD64};
-    for (int k : kinds64) occ = std::min(occ, max_active(p, k, p->R64, kernel_smem(k, p->R64, p->NT, p->EC)));
-    if (p->mode == SIP_MODE_F32_REFINED) {
-      const int kinds32[] = {K_FWD32Z, sym ? K_FWD32S : K_FWD32, K_BWD32, K_BWD32Z, K_BWD32U, K_BWD32ZU};
-      for (int k : kinds32) occ = std::min(occ, max_active(p, k, p->R32, kernel_smem(k, p->R32, p->NT, p->EC)));
+    for (int kind = 0; kind < K_NKINDS; ++kind) {
+      int bestR = 0, bestCap = -1;
+      for (int R : {6, 3}) {
+        const size_t smem = kernel_smem(kind, R, p->NT, p->EC, p->FS);
+        if (smem + ctx->kernel_static_smem > ctx->smem_optin) continue;
+        const int cap = ctx->nsm * max_active(p, kind, R, smem);
+        if (cap >= p->ntiles) { bestR = R; bestCap = cap; break; }
+        if (cap > bestCap) { bestR = R; bestCap = cap; }
+      }
+      if (bestCap < 1) {
+        free_plan_memory(p);
+        delete p;
+        return fail(ctx, SIP_ERR_INVALID_ARG, "tile shape does not fit on an SM");
+      }
+      p->Rk[kind] = bestR;
+      p->gridk[kind] = bestCap;
     }
-    if (occ < 1) {
-      free_plan_memory(p);
-      delete p;
-      return fail(ctx, SIP_ERR_INVALID_ARG, "tile shape does not fit on an SM");
-    }
-    p->grid_t = std::max(1, std::min(p->ntiles, ctx->nsm * occ));
   }
   // A into the plan layout; coefficients that point out of their block are zeroed
   {
@@ -596,7 +653,7 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
       fp.f32[q] = p->F32[q];
     }
     fp.alpha = opt.alpha;
-    e = launch(p, K_FACTOR, p->R64, fp, true);
+    e = launch(p, K_FACTOR, fp);
     if (e != cudaSuccess) return bail(e, "factor launch");
     int rc = check_status(p);
     if (rc != SIP_OK) {
@@ -705,6 +762,54 @@ int sip_plane_layout(int nx, int ny, int nz, int32_t *rbT) {
   build_rowbase(nx, ny, nz, t);
   std::memcpy(rbT, t.data(), t.size() * sizeof(int));
   return SIP_OK;
+}
+
+int sip_profile_enable(sip_plan *p, int enable) {
+  if (!p) return SIP_ERR_INVALID_ARG;
+  p->prof = enable != 0;
+  return SIP_OK;
+}
+
+int sip_profile_read(sip_plan *p, int nkinds, double *ms, int64_t *counts, int reset) {
+  if (!p || nkinds < 0) return SIP_ERR_INVALID_ARG;
+  sip_ctx *ctx = p->ctx;
+  CU(cudaStreamSynchronize(ctx->stream));
+  for (auto &r : p->recs) {
+    float t = 0.f;
+    CU(cudaEventElapsedTime(&t, r.a, r.b));
+    p->prof_ms[r.kind] += t;
+    p->prof_n[r.kind] += 1;
+    p->pool.push_back(r.a);
+    p->pool.push_back(r.b);
+  }
+  p->recs.clear();
+  for (int k = 0; k < nkinds && k <= K_NKINDS; ++k) {
+    if (ms) ms[k] = p->prof_ms[k];
+    if (counts) counts[k] = p->prof_n[k];
+  }
+  if (reset) {
+    for (int k = 0; k <= K_NKINDS; ++k) {
+      p->prof_ms[k] = 0;
+      p->prof_n[k] = 0;
+    }
+  }
+  return SIP_OK;
+}
+
+int sip_launch_count(sip_plan *p, int64_t *count_out) {
+  if (!p || !count_out) return SIP_ERR_INVALID_ARG;
+  *count_out = p->launches;
+  return SIP_OK;
+}
+
+const char *sip_kernel_name(int kind) {
+  static const char *names[] = {"factor", "fwd64", "fwd64_sym", "bwd64", "fwd32", "fwd32_sym", "fwd32_x0",
+                                "fwd32_norm", "fwd32_sym_norm", "bwd32", "bwd32_x0", "bwd32_upd64",
+                                "bwd32_x0_upd64", "resid64", "resid64_sym", "resid64_a32", "resid64_a32_sym",
+                                "utility"};
+  static_assert(sizeof(names) / sizeof(names[0]) == K_NKINDS + 1, "kernel names");
+  if (kind < 0 || kind > K_NKINDS) return nullptr;
+  return names[kind];
 }
 
 int sip_plan_bytes(sip_plan *p, size_t *bytes_out) {

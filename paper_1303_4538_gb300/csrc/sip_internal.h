@@ -57,6 +57,7 @@ struct SweepCommon {
   const Tile *tiles;   // tiles in claim order
   int ntiles;
   int exch_cells;      // max over blocks of (TJ + 2) * (TK + 2)
+  int face_slots;      // max over blocks of TJ + TK (consumer records staged per step)
   int *ticket;         // claim counter, zero at launch
   int *reset_ticket;   // counter this launch zeroes for the next launch (nullable)
   Ctl *ctl;            // epochs, done flag
@@ -107,25 +108,6 @@ struct ResParams {  // FP64 residual r = b - A x of the refinement loop (no recu
   float *r32;
   double *partials;
 };
-
-// ---- launchers (sip_k64.cu / sip_k32.cu)
-struct LaunchCfg {
-  int grid, block;
-  size_t smem;
-  cudaStream_t stream;
-  int stages;  // 3 or 6
-};
-
-size_t fwd_smem(int elem_bytes, int nvals, int nthreads, int stages, int exch_cells, int nexch);
-int fwd_nvals(bool sym, bool zx);
-
-cudaError_t launch_factor(const FacParams &p, const LaunchCfg &cfg);
-cudaError_t launch_fwd64(const FwdParams<double> &p, bool sym, const LaunchCfg &cfg);
-cudaError_t launch_bwd64(const BwdParams<double> &p, const LaunchCfg &cfg);
-cudaError_t launch_fwd32(const FwdParams<float> &p, bool sym, bool zx, bool norm, const LaunchCfg &cfg);
-cudaError_t launch_bwd32(const BwdParams<float> &p, bool zx, bool upd64, const LaunchCfg &cfg);
-cudaError_t launch_resid64(const ResParams<double> &p, bool sym, const LaunchCfg &cfg);
-cudaError_t launch_resid32a(const ResParams<float> &p, bool sym, const LaunchCfg &cfg);
 
 // utilities (sip_util.cu)
 cudaError_t launch_to_plan_f64(const void *src, int src_is_f32, double *dst, const DevBlock &hb,

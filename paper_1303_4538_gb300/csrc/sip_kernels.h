@@ -28,9 +28,9 @@ enum KernelKind {
 };
 
 const void *kernel_ptr(int kind, int stages);
-// dynamic shared memory of a launch with `nthreads` threads per CTA and an
-// exchange area of `exch_cells` cells
-size_t kernel_smem(int kind, int stages, int nthreads, int exch_cells);
+// dynamic shared memory of a launch with `nthreads` threads per CTA, an
+// exchange area of `exch_cells` cells and `face_slots` staged face records
+size_t kernel_smem(int kind, int stages, int nthreads, int exch_cells, int face_slots);
 bool kernel_is_ticketed(int kind);
 
 const void *kernel_ptr_64(int kind, int stages);

@@ -17,11 +17,17 @@
 //     ahead of use; invalid cells are zero-filled, so the arithmetic runs
 //     without branches and inactive threads produce zeros;
 //   * between tiles, the recurrence's boundary values travel through "faces":
-//     8-byte words whose upper half is the launch's epoch tag.  A producer
-//     stores them with st.relaxed.gpu, a consumer polls with ld.relaxed.gpu
-//     until the tag matches; each word is self-validating, so no fence or
-//     flag is needed.  Every wait is bounded (max_spin polls), then the kernel
-//     records DEV_TIMEOUT and runs to the end without waiting again;
+//     16-byte records of two 8-byte words whose upper halves carry the
+//     launch's epoch tag.  A producer stores a record with one st.relaxed.gpu;
+//     a consumer prefetches it with cp.async.cg into a shared-memory ring
+//     together with the step's other data and accepts it when every tag
+//     matches (each word is self-validating, so no fence or flag is needed);
+//     a stale record is re-read from L2 with ld.relaxed.gpu until it matches.
+//     Before a tile starts, one thread waits until the upstream tiles are a
+//     few steps ahead ("slack"), so the prefetched records are normally valid
+//     and no step pays an L2 round trip.  Every wait is bounded (max_spin
+//     polls), then the kernel records DEV_TIMEOUT and runs to the end
+//     without waiting again;
 //   * CTAs claim tiles with an atomic ticket in a dependency-respecting order,
 //     so a tile only waits for tiles claimed earlier by running CTAs.
 #pragma once
@@ -43,14 +49,17 @@ __device__ __forceinline__ void cp_async_zfill(void *sdst, const void *gsrc, boo
                "n"(BYTES), "r"(valid ? BYTES : 0)
                : "memory");
 }
+__device__ __forceinline__ void cp_async_16_l2(void *sdst, const void *gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-__device__ __forceinline__ void st_relaxed(uint64_t *p, uint64_t v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void st_relaxed_v2(uint64_t *p, uint64_t a, uint64_t b) {
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
 }
 __device__ __forceinline__ uint64_t ld_relaxed(const uint64_t *p) {
   uint64_t v;
@@ -63,47 +72,50 @@ __device__ __forceinline__ int ld_relaxed(const int *p) {
   return v;
 }
 
-// ---------------------------------------------------------------- face codec
-// A value travels as W words; each word = (payload32, epoch32).
+// ---------------------------------------------------------------- faces
+// A face value is a 16-byte record (two words, each = payload32 | epoch32 << 32).
 template <typename T>
 struct Face;
 template <>
 struct Face<float> {
-  static constexpr int W = 1;
   __device__ static void put(uint64_t *p, float v, unsigned ep) {
-    st_relaxed(p, ((uint64_t)ep << 32) | (uint64_t)__float_as_uint(v));
+    const uint64_t tag = (uint64_t)ep << 32;
+    st_relaxed_v2(p, tag | (uint64_t)__float_as_uint(v), tag);
   }
   __device__ static float get(const uint64_t *w) { return __uint_as_float((unsigned)w[0]); }
 };
 template <>
 struct Face<double> {
-  static constexpr int W = 2;
   __device__ static void put(uint64_t *p, double v, unsigned ep) {
+    const uint64_t tag = (uint64_t)ep << 32;
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    st_relaxed(p, ((uint64_t)ep << 32) | (b & 0xffffffffull));
-    st_relaxed(p + 1, ((uint64_t)ep << 32) | (b >> 32));
+    st_relaxed_v2(p, tag | (b & 0xffffffffull), tag | (b >> 32));
   }
   __device__ static double get(const uint64_t *w) {
     return __longlong_as_double((long long)((w[0] & 0xffffffffull) | (w[1] << 32)));
   }
 };
 
-// Poll NW tagged words until every tag equals `expect`.  Returns false (and
-// zero words) after max_spin polls or once another thread recorded an error;
-// `abort` then stays set so this thread never waits again in this launch.
-template <int NW>
-__device__ __forceinline__ bool face_wait(const uint64_t *p, unsigned expect, uint64_t (&w)[NW],
-                                          const SweepCommon &c, bool &abort) {
+template <int W>
+__device__ __forceinline__ bool rec_ok(const uint64_t (&w)[W], unsigned expect) {
+  bool ok = true;
+#pragma unroll
+  for (int q = 0; q < W; ++q) ok = ok && ((unsigned)(w[q] >> 32) == expect);
+  return ok;
+}
+
+// Poll a W-word record in L2 until every tag equals `expect`.  Returns false
+// (and zero words) after max_spin polls or once another thread recorded an
+// error; `abort` then stays set so this thread never waits again.
+template <int W>
+__device__ __noinline__ bool face_wait(const uint64_t *p, unsigned expect, uint64_t (&w)[W],
+                                       const SweepCommon &c, bool &abort) {
   if (!abort) {
     long long spins = 0;
     for (;;) {
-      bool ok = true;
 #pragma unroll
-      for (int q = 0; q < NW; ++q) {
-        w[q] = ld_relaxed(p + q);
-        ok = ok && ((unsigned)(w[q] >> 32) == expect);
-      }
-      if (ok) return true;
+      for (int q = 0; q < W; ++q) w[q] = ld_relaxed(p + q);
+      if (rec_ok<W>(w, expect)) return true;
       ++spins;
       if (spins > c.max_spin) {
         atomicCAS(c.status, DEV_OK, DEV_TIMEOUT);
@@ -118,8 +130,23 @@ __device__ __forceinline__ bool face_wait(const uint64_t *p, unsigned expect, ui
     }
   }
 #pragma unroll
-  for (int q = 0; q < NW; ++q) w[q] = 0;
+  for (int q = 0; q < W; ++q) w[q] = 0;
   return false;
+}
+
+// Take the record staged in shared memory; re-read it from L2 if it is stale.
+template <int W>
+__device__ __forceinline__ void rec_take(const uint64_t *staged, const uint64_t *g, unsigned expect,
+                                         uint64_t (&w)[W], const SweepCommon &c, bool &abort) {
+#pragma unroll
+  for (int q = 0; q < W; ++q) w[q] = staged[q];
+  if (!rec_ok<W>(w, expect)) face_wait<W>(g, expect, w, c, abort);
+}
+
+template <int W>
+__device__ __forceinline__ void rec_prefetch(uint64_t *sdst, const uint64_t *g) {
+#pragma unroll
+  for (int q = 0; q < W; q += 2) cp_async_16_l2(sdst + q, g + q);
 }
 
 // Face storage of one tile: J face [nsteps_max][TK][W], then K face
@@ -172,7 +199,7 @@ __device__ __forceinline__ double block_sum(double v, double *s_red) {
 }
 
 struct ColGeom {
-  int dj, dk, j0, k0, j, k, nsteps, s0;
+  int dj, dk, j0, k0, j, k, nsteps, s0, njt, nkt;
   bool col, hasS, hasN, hasB, hasT;
   __device__ ColGeom(const DevBlock &B, const Tile &tl) {
     dj = threadIdx.x % B.TJ;
@@ -182,7 +209,8 @@ struct ColGeom {
     j = j0 + dj;
     k = k0 + dk;
     col = (j < B.ny) && (k < B.nz) && (dk < B.TK);
-    const int njt = min(B.TJ, B.ny - j0), nkt = min(B.TK, B.nz - k0);
+    njt = min(B.TJ, B.ny - j0);
+    nkt = min(B.TK, B.nz - k0);
     nsteps = B.nx + njt + nkt - 2;
     s0 = j0 + k0;
     hasS = j0 > 0;
@@ -192,6 +220,36 @@ struct ColGeom {
   }
 };
 
+// Shared-memory carve-up of a sweep kernel: stage ring, exchange buffer, face ring.
+template <typename T>
+struct Smem {
+  T *stage;       // [R][NV][NT]
+  T *exch;        // [2][NE][EC]
+  uint64_t *fst;  // [R][FS][W]
+  __device__ Smem(unsigned char *raw, int R, int NV, int NT, int NE, int EC) {
+    stage = reinterpret_cast<T *>(raw);
+    size_t off = (size_t)R * NV * NT * sizeof(T);
+    exch = reinterpret_cast<T *>(raw + off);
+    off += (size_t)2 * NE * EC * sizeof(T);
+    off = (off + 15) & ~(size_t)15;
+    fst = reinterpret_cast<uint64_t *>(raw + off);
+  }
+};
+
+// Slack gate: before a tile starts, wait until the records that the tile will
+// consume `lead` steps after its first need are published, so the records
+// prefetched during the walk are normally already valid.
+template <int W>
+__device__ __forceinline__ void slack_gate(const uint64_t *recJ, const uint64_t *recK, unsigned expect,
+                                           const SweepCommon &c, bool &abort) {
+  if (threadIdx.x == 0) {
+    uint64_t w[W];
+    if (recJ) face_wait<W>(recJ, expect, w, c, abort);
+    if (recK) face_wait<W>(recK, expect, w, c, abort);
+  }
+  __syncthreads();
+}
+
 // ============================================================== factorisation
 // Stone's factorisation, per cell after W, S, B (lu3d):
 //   LB = AB / (1 + a (UN_B + UE_B)),  LW = AW / (1 + a (UN_W + UT_W)),
@@ -199,21 +257,20 @@ struct ColGeom {
 //   P1 = a (LB UN_B + LW UN_W),  P2 = a (LB UE_B + LS UE_S),  P3 = a (LW UT_W + LS UT_S),
 //   LP = AP + P1 + P2 + P3 - LB UT_B - LW UE_W - LS UN_S,
 //   UN = (AN - P1) / LP,  UE = (AE - P2) / LP,  UT = (AT - P3) / LP.
-// Stored: LB, LW, LS, 1/LP, UN, UE, UT.
+// Stored: LB, LW, LS, 1/LP, UN, UE, UT.  Faces carry (UN, UE, UT): 48 bytes.
 template <int R>
 __global__ void __launch_bounds__(512) k_factor(FacParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_claim;
-  constexpr int NV = 7;
+  constexpr int NV = 7, W = 6;
   const SweepCommon &c = P.c;
   const unsigned ep = sweep_prologue(c);
   // block-uniform exit decision (the status word may change during the launch)
   if (__syncthreads_or(ld_relaxed(c.status) != DEV_OK)) return;
   const unsigned expect = ep + (c.stall ? 0x40000000u : 0u);
   const int NT = blockDim.x, tid = threadIdx.x;
-  double *stage = reinterpret_cast<double *>(smem_raw);
-  double *exch = stage + (size_t)R * NV * NT;  // [2][3][exch_cells]
-  const int EC = c.exch_cells;
+  const int EC = c.exch_cells, FS = c.face_slots;
+  Smem<double> sm(smem_raw, R, NV, NT, 3, EC);
   bool abort = false;
 
   for (;;) {
@@ -228,15 +285,24 @@ __global__ void __launch_bounds__(512) k_factor(FacParams P) {
     uint64_t *upK = g.hasB ? tile_faces(c, B, tl.gtile - B.nTJ) : nullptr;
     const int TJ2 = B.TJ + 2;
     const int me = (g.dk + 1) * TJ2 + g.dj + 1;
+    const bool cJ = g.dj == 0 && g.hasS, cK = g.dk == 0 && g.hasB;  // face consumers
+    {
+      const int lead = min(R + 1, B.nx - 1);
+      slack_gate<W>(upJ ? faceJ(upJ, B, lead + B.TJ - 1, 0, W) : nullptr,
+                    upK ? faceK(upK, B, lead + B.TK - 1, 0, W) : nullptr, expect, c, abort);
+    }
 
     auto issue = [&](int tt) {
       if (tt < g.nsteps) {
         const int i = tt - g.dj - g.dk;
         const bool v = g.col && i >= 0 && i < B.nx;
         const long long a = v ? B.cell0 + rbk[g.s0 + tt] + g.j : 0;
-        double *st = stage + (size_t)(tt % R) * NV * NT + tid;
+        double *st = sm.stage + (size_t)(tt % R) * NV * NT + tid;
 #pragma unroll
         for (int q = 0; q < NV; ++q) cp_async_zfill<8>(st + q * NT, P.a[q] + a, v);
+        uint64_t *fs = sm.fst + (size_t)(tt % R) * FS * W;
+        if (cJ && v) rec_prefetch<W>(fs + g.dk * W, faceJ(upJ, B, tt + B.TJ - 1, g.dk, W));
+        if (cK && v) rec_prefetch<W>(fs + (B.TK + g.dj) * W, faceK(upK, B, tt + B.TK - 1, g.dj, W));
       }
       cp_async_commit();
     };
@@ -248,38 +314,28 @@ __global__ void __launch_bounds__(512) k_factor(FacParams P) {
     for (int t = 0; t < g.nsteps; ++t) {
       issue(t + R - 1);
       cp_async_wait<R - 1>();
-      const double *st = stage + (size_t)(t % R) * NV * NT + tid;
+      const double *st = sm.stage + (size_t)(t % R) * NV * NT + tid;
+      const uint64_t *fs = sm.fst + (size_t)(t % R) * FS * W;
       const int i = t - g.dj - g.dk;
       const bool act = g.col && i >= 0 && i < B.nx;
-      double *E = exch + (size_t)(t & 1) * 3 * EC;
+      double *E = sm.exch + (size_t)(t & 1) * 3 * EC;
       E[me] = unW;
       E[EC + me] = ueW;
       E[2 * EC + me] = utW;
       if (g.dj == 0) {
-        double h[3] = {0, 0, 0};
-        if (act && g.hasS) {
-          uint64_t w[6];
-          face_wait<6>(faceJ(upJ, B, t + B.TJ - 1, g.dk, 6), expect, w, c, abort);
-          h[0] = Face<double>::get(w);
-          h[1] = Face<double>::get(w + 2);
-          h[2] = Face<double>::get(w + 4);
-        }
-        E[me - 1] = h[0];
-        E[EC + me - 1] = h[1];
-        E[2 * EC + me - 1] = h[2];
+        uint64_t w[W] = {0, 0, 0, 0, 0, 0};
+        if (act && cJ) rec_take<W>(fs + g.dk * W, faceJ(upJ, B, t + B.TJ - 1, g.dk, W), expect, w, c, abort);
+        E[me - 1] = Face<double>::get(w);
+        E[EC + me - 1] = Face<double>::get(w + 2);
+        E[2 * EC + me - 1] = Face<double>::get(w + 4);
       }
       if (g.dk == 0) {
-        double h[3] = {0, 0, 0};
-        if (act && g.hasB) {
-          uint64_t w[6];
-          face_wait<6>(faceK(upK, B, t + B.TK - 1, g.dj, 6), expect, w, c, abort);
-          h[0] = Face<double>::get(w);
-          h[1] = Face<double>::get(w + 2);
-          h[2] = Face<double>::get(w + 4);
-        }
-        E[me - TJ2] = h[0];
-        E[EC + me - TJ2] = h[1];
-        E[2 * EC + me - TJ2] = h[2];
+        uint64_t w[W] = {0, 0, 0, 0, 0, 0};
+        if (act && cK)
+          rec_take<W>(fs + (B.TK + g.dj) * W, faceK(upK, B, t + B.TK - 1, g.dj, W), expect, w, c, abort);
+        E[me - TJ2] = Face<double>::get(w);
+        E[EC + me - TJ2] = Face<double>::get(w + 2);
+        E[2 * EC + me - TJ2] = Face<double>::get(w + 4);
       }
       __syncthreads();
       const double unS = E[me - 1], ueS = E[EC + me - 1], utS = E[2 * EC + me - 1];
@@ -311,13 +367,13 @@ __global__ void __launch_bounds__(512) k_factor(FacParams P) {
           for (int q = 0; q < 7; ++q) P.f32[q][a] = (float)outv[q];
         }
         if (g.dj == B.TJ - 1 && g.hasN) {
-          uint64_t *f = faceJ(myf, B, t, g.dk, 6);
+          uint64_t *f = faceJ(myf, B, t, g.dk, W);
           Face<double>::put(f, UN, ep);
           Face<double>::put(f + 2, UE, ep);
           Face<double>::put(f + 4, UT, ep);
         }
         if (g.dk == B.TK - 1 && g.hasT) {
-          uint64_t *f = faceK(myf, B, t, g.dj, 6);
+          uint64_t *f = faceK(myf, B, t, g.dj, W);
           Face<double>::put(f, UN, ep);
           Face<double>::put(f + 2, UE, ep);
           Face<double>::put(f + 4, UT, ep);
@@ -354,20 +410,20 @@ struct FwdSlots {
 
 template <typename T, bool SYM, bool ZX, bool NORM, int R>
 __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
+  static_assert(!(SYM && ZX), "x = 0 needs no matrix");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_claim;
   __shared__ double s_red[32];
   using S = FwdSlots<SYM, ZX>;
-  constexpr int NV = S::NV, NE = S::NE;
+  constexpr int NV = S::NV, NE = S::NE, W = 2;
   const SweepCommon &c = P.c;
   const unsigned ep = sweep_prologue(c);
   // block-uniform exit decision (the status word may change during the launch)
   if (__syncthreads_or(c.ctl->done || ld_relaxed(c.status) != DEV_OK)) return;
   const unsigned expect = ep + (c.stall ? 0x40000000u : 0u);
   const int NT = blockDim.x, tid = threadIdx.x;
-  T *stage = reinterpret_cast<T *>(smem_raw);
-  T *exch = stage + (size_t)R * NV * NT;  // [2][NE][exch_cells]
-  const int EC = c.exch_cells;
+  const int EC = c.exch_cells, FS = c.face_slots;
+  Smem<T> sm(smem_raw, R, NV, NT, NE, EC);
   const T *src[S::NA > 0 ? S::NA : 1];
   if constexpr (!ZX) {
     if constexpr (SYM) {
@@ -395,6 +451,12 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
     const int TJ2 = B.TJ + 2;
     const int me = (g.dk + 1) * TJ2 + g.dj + 1;
     const bool eS = g.dj == 0, eN = g.dj == B.TJ - 1, eB = g.dk == 0, eT = g.dk == B.TK - 1;
+    const bool cJ = eS && g.hasS, cK = eB && g.hasB;  // face consumers
+    {
+      const int lead = min(R + 1, B.nx - 1);
+      slack_gate<W>(upJ ? faceJ(upJ, B, lead + B.TJ - 1, 0, W) : nullptr,
+                    upK ? faceK(upK, B, lead + B.TK - 1, 0, W) : nullptr, expect, c, abort);
+    }
 
     auto issue = [&](int tt) {
       if (tt < g.nsteps) {
@@ -402,7 +464,7 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
         const int s = g.s0 + tt;
         const bool v = g.col && i >= 0 && i < B.nx;
         const long long a = v ? B.cell0 + rbk[s] + g.j : 0;
-        T *st = stage + (size_t)(tt % R) * NV * NT + tid;
+        T *st = sm.stage + (size_t)(tt % R) * NV * NT + tid;
         if constexpr (!ZX) {
 #pragma unroll
           for (int q = 0; q < S::NA; ++q) cp_async_zfill<EB>(st + q * NT, src[q] + a, v);
@@ -432,6 +494,9 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
             cp_async_zfill<EB>(st + S::HATB * NT, P.at + hk, vk && eB);
           }
         }
+        uint64_t *fs = sm.fst + (size_t)(tt % R) * FS * W;
+        if (cJ && v) rec_prefetch<W>(fs + g.dk * W, faceJ(upJ, B, tt + B.TJ - 1, g.dk, W));
+        if (cK && v) rec_prefetch<W>(fs + (B.TK + g.dj) * W, faceK(upK, B, tt + B.TK - 1, g.dj, W));
       }
       cp_async_commit();
     };
@@ -448,10 +513,11 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
     for (int t = 0; t < g.nsteps; ++t) {
       issue(t + R - 1);
       cp_async_wait<R - 1>();
-      const T *st = stage + (size_t)(t % R) * NV * NT + tid;
+      const T *st = sm.stage + (size_t)(t % R) * NV * NT + tid;
+      const uint64_t *fs = sm.fst + (size_t)(t % R) * FS * W;
       const int i = t - g.dj - g.dk;
       const bool act = g.col && i >= 0 && i < B.nx;
-      T *E = exch + (size_t)(t & 1) * NE * EC;
+      T *E = sm.exch + (size_t)(t & 1) * NE * EC;
       T *EY = E + (ZX ? 0 : 2) * EC;  // ym1 plane
       T xp1 = 0;
       if constexpr (!ZX) {
@@ -465,13 +531,9 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
       }
       EY[me] = ym1;
       if (eS) {
-        T hy = 0;
-        if (act && g.hasS) {
-          uint64_t w[Face<T>::W];
-          face_wait<Face<T>::W>(faceJ(upJ, B, t + B.TJ - 1, g.dk, Face<T>::W), expect, w, c, abort);
-          hy = Face<T>::get(w);
-        }
-        EY[me - 1] = hy;
+        uint64_t w[W] = {0, 0};
+        if (act && cJ) rec_take<W>(fs + g.dk * W, faceJ(upJ, B, t + B.TJ - 1, g.dk, W), expect, w, c, abort);
+        EY[me - 1] = Face<T>::get(w);
         if constexpr (!ZX) {
           E[me - 1] = st[S::HXJ * NT];
           if constexpr (SYM) E[3 * EC + me - 1] = st[S::HANS * NT];
@@ -482,13 +544,10 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
         if (eT) E[EC + me + TJ2] = st[S::HXK * NT];
       }
       if (eB) {
-        T hy = 0;
-        if (act && g.hasB) {
-          uint64_t w[Face<T>::W];
-          face_wait<Face<T>::W>(faceK(upK, B, t + B.TK - 1, g.dj, Face<T>::W), expect, w, c, abort);
-          hy = Face<T>::get(w);
-        }
-        EY[me - TJ2] = hy;
+        uint64_t w[W] = {0, 0};
+        if (act && cK)
+          rec_take<W>(fs + (B.TK + g.dj) * W, faceK(upK, B, t + B.TK - 1, g.dj, W), expect, w, c, abort);
+        EY[me - TJ2] = Face<T>::get(w);
         if constexpr (!ZX) {
           E[me - TJ2] = st[S::HXK * NT];
           if constexpr (SYM) E[4 * EC + me - TJ2] = st[S::HATB * NT];
@@ -530,8 +589,8 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
       if (act) {
         const long long a = B.cell0 + rbk[g.s0 + t] + g.j;
         P.y[a] = y;
-        if (eN && g.hasN) Face<T>::put(faceJ(myf, B, t, g.dk, Face<T>::W), y, ep);
-        if (eT && g.hasT) Face<T>::put(faceK(myf, B, t, g.dj, Face<T>::W), y, ep);
+        if (eN && g.hasN) Face<T>::put(faceJ(myf, B, t, g.dk, W), y, ep);
+        if (eT && g.hasT) Face<T>::put(faceK(myf, B, t, g.dj, W), y, ep);
       }
       xm1 = x0;
       x0 = xp1;
@@ -549,20 +608,22 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
 // =========================================================== backward sweep
 // backward3d with the update: d_P = y_P - UE d_E - UN d_N - UT d_T
 // (descending planes), x_P <- x_P + d_P.  ZX: x = 0 on entry (x_P <- d_P).
-// UPD64 (refined mode, last inner iteration): also x64_P += (double) x_P.
+// UPD64 (refined mode, last inner iteration): x64_P += (double) x_P instead
+// of storing x_P.
 template <typename T, bool ZX, bool UPD64, int R>
 __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_claim;
   constexpr int NV = (ZX ? 4 : 5) + (UPD64 ? 2 : 0);  // ue un ut y [x] [x64 as 2 slots]
+  constexpr int W = 2;
   const SweepCommon &c = P.c;
   const unsigned ep = sweep_prologue(c);
   // block-uniform exit decision (the status word may change during the launch)
   if (__syncthreads_or(c.ctl->done || ld_relaxed(c.status) != DEV_OK)) return;
   const unsigned expect = ep + (c.stall ? 0x40000000u : 0u);
   const int NT = blockDim.x, tid = threadIdx.x;
-  T *stage = reinterpret_cast<T *>(smem_raw);
-  T *exch = stage + (size_t)R * NV * NT;  // [2][exch_cells]
+  const int EC = c.exch_cells, FS = c.face_slots;
+  Smem<T> sm(smem_raw, R, NV, NT, 1, EC);
   constexpr int EB = (int)sizeof(T);
   bool abort = false;
 
@@ -578,8 +639,16 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
     uint64_t *dnK = g.hasT ? tile_faces(c, B, tl.gtile + B.nTJ) : nullptr;
     const int TJ2 = B.TJ + 2;
     const int me = (g.dk + 1) * TJ2 + g.dj + 1;
-    const int EC = c.exch_cells;
     const int last = g.nsteps - 1;
+    const bool cJ = g.dj == B.TJ - 1 && g.hasN, cK = g.dk == B.TK - 1 && g.hasT;  // face consumers
+    {
+      // the consumer of the last valid row (column) needs, `lead` steps into
+      // the walk, cell i = nx-1-lead, published on the producer's step i + lane
+      const int lead = min(R + 1, B.nx - 1);
+      const int i = B.nx - 1 - lead;
+      slack_gate<W>(dnJ ? faceJ(dnJ, B, i + g.nkt - 1, g.nkt - 1, W) : nullptr,
+                    dnK ? faceK(dnK, B, i + g.njt - 1, g.njt - 1, W) : nullptr, expect, c, abort);
+    }
 
     // backward step u processes local plane t = last - u
     auto issue = [&](int uu) {
@@ -588,16 +657,19 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
         const int i = t - g.dj - g.dk;
         const bool v = g.col && i >= 0 && i < B.nx;
         const long long a = v ? B.cell0 + rbk[g.s0 + t] + g.j : 0;
-        T *st = stage + (size_t)(uu % R) * NV * NT + tid;
+        T *st = sm.stage + (size_t)(uu % R) * NV * NT + tid;
         cp_async_zfill<EB>(st, P.ue + a, v);
         cp_async_zfill<EB>(st + NT, P.un + a, v);
         cp_async_zfill<EB>(st + 2 * NT, P.ut + a, v);
         cp_async_zfill<EB>(st + 3 * NT, P.y + a, v);
         if constexpr (!ZX) cp_async_zfill<EB>(st + 4 * NT, P.x + a, v);
         if constexpr (UPD64) {
-          double *s64 = reinterpret_cast<double *>(stage + (size_t)(uu % R) * NV * NT + (NV - 2) * NT) + tid;
+          double *s64 = reinterpret_cast<double *>(sm.stage + (size_t)(uu % R) * NV * NT + (NV - 2) * NT) + tid;
           cp_async_zfill<8>(s64, P.x64 + a, v);
         }
+        uint64_t *fs = sm.fst + (size_t)(uu % R) * FS * W;
+        if (cJ && v) rec_prefetch<W>(fs + g.dk * W, faceJ(dnJ, B, t - (B.TJ - 1), g.dk, W));
+        if (cK && v) rec_prefetch<W>(fs + (B.TK + g.dj) * W, faceK(dnK, B, t - (B.TK - 1), g.dj, W));
       }
       cp_async_commit();
     };
@@ -608,29 +680,23 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
     for (int u = 0; u < g.nsteps; ++u) {
       issue(u + R - 1);
       cp_async_wait<R - 1>();
-      const T *st = stage + (size_t)(u % R) * NV * NT + tid;
+      const T *st = sm.stage + (size_t)(u % R) * NV * NT + tid;
+      const uint64_t *fs = sm.fst + (size_t)(u % R) * FS * W;
       const int t = last - u;
       const int i = t - g.dj - g.dk;
       const bool act = g.col && i >= 0 && i < B.nx;
-      T *E = exch + (size_t)(u & 1) * EC;
+      T *E = sm.exch + (size_t)(u & 1) * EC;
       E[me] = dE;
       if (g.dj == B.TJ - 1) {
-        T h = 0;
-        if (act && g.hasN) {
-          uint64_t w[Face<T>::W];
-          face_wait<Face<T>::W>(faceJ(dnJ, B, t - (B.TJ - 1), g.dk, Face<T>::W), expect, w, c, abort);
-          h = Face<T>::get(w);
-        }
-        E[me + 1] = h;
+        uint64_t w[W] = {0, 0};
+        if (act && cJ) rec_take<W>(fs + g.dk * W, faceJ(dnJ, B, t - (B.TJ - 1), g.dk, W), expect, w, c, abort);
+        E[me + 1] = Face<T>::get(w);
       }
       if (g.dk == B.TK - 1) {
-        T h = 0;
-        if (act && g.hasT) {
-          uint64_t w[Face<T>::W];
-          face_wait<Face<T>::W>(faceK(dnK, B, t - (B.TK - 1), g.dj, Face<T>::W), expect, w, c, abort);
-          h = Face<T>::get(w);
-        }
-        E[me + TJ2] = h;
+        uint64_t w[W] = {0, 0};
+        if (act && cK)
+          rec_take<W>(fs + (B.TK + g.dj) * W, faceK(dnK, B, t - (B.TK - 1), g.dj, W), expect, w, c, abort);
+        E[me + TJ2] = Face<T>::get(w);
       }
       __syncthreads();
       const T dN = E[me + 1], dT = E[me + TJ2];
@@ -642,13 +708,14 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
         T xn = d;
         if constexpr (!ZX) xn = st[4 * NT] + d;
         if constexpr (UPD64) {
-          const double *s64 = reinterpret_cast<const double *>(stage + (size_t)(u % R) * NV * NT + (NV - 2) * NT) + tid;
+          const double *s64 =
+              reinterpret_cast<const double *>(sm.stage + (size_t)(u % R) * NV * NT + (NV - 2) * NT) + tid;
           P.x64[a] = *s64 + (double)xn;
         } else {
           P.x[a] = xn;
         }
-        if (g.dj == 0 && g.hasS) Face<T>::put(faceJ(myf, B, t, g.dk, Face<T>::W), d, ep);
-        if (g.dk == 0 && g.hasB) Face<T>::put(faceK(myf, B, t, g.dj, Face<T>::W), d, ep);
+        if (g.dj == 0 && g.hasS) Face<T>::put(faceJ(myf, B, t, g.dk, W), d, ep);
+        if (g.dk == 0 && g.hasB) Face<T>::put(faceK(myf, B, t, g.dj, W), d, ep);
       }
       dE = act ? d : T(0);
     }

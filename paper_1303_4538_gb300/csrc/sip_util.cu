@@ -20,22 +20,27 @@ bool kernel_is_ticketed(int kind) {
 
 static size_t a16(size_t b) { return (b + 15) & ~(size_t)15; }
 
-size_t kernel_smem(int kind, int R, int NT, int EC) {
-  const size_t nt = (size_t)NT, ec = (size_t)EC, r = (size_t)R;
+// stage ring + exchange buffer (+ face ring), laid out as in sip_sweeps.cuh
+static size_t sweep_bytes(size_t r, size_t nv, size_t nt, size_t ne, size_t ec, size_t eb, size_t fs, size_t w) {
+  return a16(r * nv * nt * eb + 2 * ne * ec * eb) + r * fs * w * 8;
+}
+
+size_t kernel_smem(int kind, int R, int NT, int EC, int FS) {
+  const size_t nt = (size_t)NT, ec = (size_t)EC, r = (size_t)R, fs = (size_t)FS;
   switch (kind) {
-    case K_FACTOR: return r * 7 * nt * 8 + 2 * 3 * ec * 8;
-    case K_FWD64: return r * 15 * nt * 8 + 2 * 3 * ec * 8;
-    case K_FWD64S: return r * 14 * nt * 8 + 2 * 5 * ec * 8;
-    case K_BWD64: return r * 5 * nt * 8 + 2 * ec * 8;
+    case K_FACTOR: return sweep_bytes(r, 7, nt, 3, ec, 8, fs, 6);
+    case K_FWD64: return sweep_bytes(r, 15, nt, 3, ec, 8, fs, 2);
+    case K_FWD64S: return sweep_bytes(r, 14, nt, 5, ec, 8, fs, 2);
+    case K_BWD64: return sweep_bytes(r, 5, nt, 1, ec, 8, fs, 2);
     case K_FWD32:
-    case K_FWD32N: return r * 15 * nt * 4 + 2 * 3 * ec * 4;
+    case K_FWD32N: return sweep_bytes(r, 15, nt, 3, ec, 4, fs, 2);
     case K_FWD32S:
-    case K_FWD32SN: return r * 14 * nt * 4 + 2 * 5 * ec * 4;
-    case K_FWD32Z: return r * 5 * nt * 4 + 2 * 1 * ec * 4;
-    case K_BWD32: return r * 5 * nt * 4 + 2 * ec * 4;
-    case K_BWD32Z: return r * 4 * nt * 4 + 2 * ec * 4;
-    case K_BWD32U: return r * 7 * nt * 4 + 2 * ec * 4;
-    case K_BWD32ZU: return r * 6 * nt * 4 + 2 * ec * 4;
+    case K_FWD32SN: return sweep_bytes(r, 14, nt, 5, ec, 4, fs, 2);
+    case K_FWD32Z: return sweep_bytes(r, 5, nt, 1, ec, 4, fs, 2);
+    case K_BWD32: return sweep_bytes(r, 5, nt, 1, ec, 4, fs, 2);
+    case K_BWD32Z: return sweep_bytes(r, 4, nt, 1, ec, 4, fs, 2);
+    case K_BWD32U: return sweep_bytes(r, 7, nt, 1, ec, 4, fs, 2);
+    case K_BWD32ZU: return sweep_bytes(r, 6, nt, 1, ec, 4, fs, 2);
     case K_RES64: return r * 4 * nt * 8 + a16(r * 7 * nt * 8) + 2 * 2 * ec * 8;
     case K_RES64S: return r * 4 * nt * 8 + a16(r * 6 * nt * 8) + 2 * 4 * ec * 8;
     case K_RES32A: return r * 4 * nt * 8 + a16(r * 7 * nt * 4) + 2 * 2 * ec * 8;

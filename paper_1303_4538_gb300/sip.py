@@ -40,7 +40,8 @@ ERROR_NAMES = {
 EXPORTED = (
     "sip_default_options", "sip_create", "sip_destroy", "sip_last_error", "sip_factor",
     "sip_iterate", "sip_solve", "sip_get_history", "sip_export_factors", "sip_plan_bytes",
-    "sip_plan_destroy", "sip_plane_layout",
+    "sip_plan_destroy", "sip_plane_layout", "sip_profile_enable", "sip_profile_read",
+    "sip_launch_count", "sip_kernel_name",
 )
 
 
@@ -103,8 +104,13 @@ def lib():
         L.sip_plan_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
         L.sip_plan_destroy.argtypes = [P]
         L.sip_plane_layout.argtypes = [I, I, I, P]
+        L.sip_profile_enable.argtypes = [P, I]
+        L.sip_profile_read.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int64), I]
+        L.sip_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+        L.sip_kernel_name.argtypes = [I]
+        L.sip_kernel_name.restype = ctypes.c_char_p
         for name in EXPORTED:
-            if name not in ("sip_default_options", "sip_last_error"):
+            if name not in ("sip_default_options", "sip_last_error", "sip_kernel_name"):
                 getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -204,6 +210,22 @@ class Plan:
         arr = (ctypes.c_void_p * 7)(*[_ptr(o) for o in outs])
         self.ctx.check(lib().sip_export_factors(self.h, int(blk), arr))
 
+    def profile(self, enable: bool = True) -> None:
+        self.ctx.check(lib().sip_profile_enable(self.h, 1 if enable else 0))
+
+    def profile_read(self, reset: bool = True):
+        """{kernel name: (total ms, launches)} since the last reset."""
+        names = kernel_names()
+        ms = (ctypes.c_double * len(names))()
+        n = (ctypes.c_int64 * len(names))()
+        self.ctx.check(lib().sip_profile_read(self.h, len(names), ms, n, 1 if reset else 0))
+        return {names[k]: (ms[k], n[k]) for k in range(len(names)) if n[k]}
+
+    def launches(self) -> int:
+        c = ctypes.c_int64(0)
+        self.ctx.check(lib().sip_launch_count(self.h, ctypes.byref(c)))
+        return c.value
+
     def nbytes(self) -> int:
         b = ctypes.c_size_t(0)
         self.ctx.check(lib().sip_plan_bytes(self.h, ctypes.byref(b)))
@@ -231,3 +253,14 @@ def plane_layout(nx: int, ny: int, nz: int):
     if rc != SIP_OK:
         raise SipError(rc, "sip_plane_layout failed")
     return out
+
+
+def kernel_names() -> List[str]:
+    out = []
+    k = 0
+    while True:
+        nm = lib().sip_kernel_name(k)
+        if nm is None:
+            return out
+        out.append(nm.decode())
+        k += 1
