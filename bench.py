@@ -40,6 +40,7 @@ METRIC = "SIP MLUP/s & %HBM roofline, FP32-refined vs FP64; p50/p99 solve latenc
 # written once; neighbour values reused on chip).  Words of 8 B (FP64) or 4 B.
 ALGO_BYTES = {
     "factor": 7 * 8 + 7 * 8,           # A in, LB LW LS 1/LP UN UE UT out
+    "factor32": 7 * 8 + 7 * 4,         # A in (FP64), FP32 factors out
     "fwd64": 14 * 8,                   # A(7) b x LB LW LS 1/LP in, y out
     "fwd64_sym": 11 * 8,               # AP AE AN AT b x LB LW LS 1/LP in, y out
     "bwd64": 6 * 8,                    # UE UN UT y x in, x out

@@ -98,7 +98,7 @@ typedef struct {
   int32_t inner_iters;     /* SIP_MODE_F32_REFINED: FP32 iterations per FP64 correction (>= 1) */
   int64_t max_spin;        /* polls before a device wait gives up (<= 0: default 2^22) */
   int32_t tile_j, tile_k;  /* column-tile shape of the sweeps (0: chosen by the autotuner) */
-  int32_t check_every;     /* reserved, must be 0 or 1 */
+  int32_t stages;          /* depth of the sweeps' shared-memory prefetch ring: 0 (auto), 4 or 6 */
   int32_t debug_stall;     /* test hook: 1 makes the sweeps wait for a tag no producer
                               writes, so the bounded waits time out (SIP_ERR_DEVICE_TIMEOUT) */
 } sip_options;
@@ -154,6 +154,18 @@ int sip_export_factors(sip_plan *plan, int blk, double *const out[7]);
  * hyperplane i+j+k = s are contiguous, rows k ascend within a plane and j
  * ascends within a row.  Entries of empty rows are INT32_MIN. */
 int sip_plane_layout(int nx, int ny, int nz, int32_t *rbT);
+
+/* Measurement aids.  sip_profile_enable(plan, 1) records a CUDA event pair
+ * on the plan's stream around every later kernel launch of the plan;
+ * sip_profile_read synchronises the stream and writes, for each kernel kind
+ * k < nkinds, the summed device time in ms (ms[k], host) and the number of
+ * timed launches (counts[k], host) since the last reset (reset != 0 clears).
+ * sip_launch_count (host out) = all kernels the plan has launched so far.
+ * sip_kernel_name(k) names kind k (NULL past the last kind). */
+int sip_profile_enable(sip_plan *plan, int enable);
+int sip_profile_read(sip_plan *plan, int nkinds, double *ms, int64_t *counts, int reset);
+int sip_launch_count(sip_plan *plan, int64_t *count_out);
+const char *sip_kernel_name(int kind);
 
 /* Total device bytes owned by the plan (host out). */
 int sip_plan_bytes(sip_plan *plan, size_t *bytes_out);

@@ -3,16 +3,18 @@
 // A plan (the paper's redesigned solver module, arXiv:1303.4538 Sec. 4.1: the
 // solver owns its coefficient arrays and computes the incomplete factorisation
 // once, before the relaxations) holds, for every block, the plane layout
-// tables, reordered copies of A, Stone's factors, the work vectors, the face
-// buffers of the sweeps and a device-resident control block.  All launches go
-// to the context's stream; the only device->host transfers are the control
-// block reads that a call needs to return its results.
+// tables, per-cell records with the reordered coefficients and Stone's
+// factors, the work vectors, the face buffers of the sweeps and a
+// device-resident control block.  All launches go to the context's stream;
+// the only device->host transfers are the control block reads that a call
+// needs to return its results.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -29,7 +31,6 @@ struct sip_ctx {
   int nsm = 0;
   size_t smem_optin = 0;
   std::string err = "no error";
-  bool attrs_set = false;
   size_t kernel_static_smem = 0;  // largest static shared memory of any sweep kernel
 };
 
@@ -51,16 +52,32 @@ int fail(sip_ctx *ctx, int code, const std::string &msg) {
     }                                                                                 \
   } while (0)
 
-struct TileShape {
-  int TJ = 32, TK = 8, R = 6;
-};
+// Plane layout tables of a block: PO[s] = first cell of plane s, F[m] = number
+// of (i, j) with i + j <= m (cells of one (j, k) cross-section diagonal).
+void build_tables(int nx, int ny, int nz, std::vector<int> &PO, std::vector<int> &F) {
+  const int np = nx + ny + nz - 2, mmax = nx + ny - 2;
+  F.assign(mmax + 1, 0);
+  long long acc = 0;
+  for (int m = 0; m <= mmax; ++m) {
+    const int lo = std::max(0, m - (nx - 1)), hi = std::min(ny - 1, m);
+    acc += std::max(0, hi - lo + 1);
+    F[m] = (int)acc;
+  }
+  PO.assign(np, 0);
+  long long off = 0;
+  for (int s = 0; s < np; ++s) {
+    PO[s] = (int)off;
+    const int klo = std::max(0, s - mmax), khi = std::min(nz - 1, s);
+    for (int k = klo; k <= khi; ++k) off += F[s - k] - (s - k > 0 ? F[s - k - 1] : 0);
+  }
+}
 
 }  // namespace
 
 struct BlockHost {
   sip_block_desc d;
-  DevBlock db;  // with device rbT
-  std::vector<int> rbT;
+  DevBlock db;
+  std::vector<int> PO, F;
   long long n = 0;
 };
 
@@ -69,22 +86,21 @@ struct sip_plan {
   sip_options opt;
   int mode = 0;
   bool sym = false;
+  bool a32in = false;
   std::vector<BlockHost> blocks;
-  std::vector<sip_interface> ifaces;
   long long ncells = 0;
   int ntiles = 0;
-  int NT = 256, EC = 0, FS = 0;
+  int Q = 2, NW = 8, NT = 256, TK = 16, tab_ints = 0;
   int Rk[K_NKINDS] = {};     // stage depth chosen per kernel kind
   int gridk[K_NKINDS] = {};  // resident CTAs per kernel kind (grid of the ticketed sweeps)
   std::vector<void *> allocs;
   size_t bytes = 0;
   DevBlock *d_blocks = nullptr;
   Tile *d_tiles_f = nullptr, *d_tiles_b = nullptr;
-  int *d_rb = nullptr;
-  double *A64[7] = {};
-  float *A32[7] = {};
-  double *F64[7] = {};
-  float *F32[7] = {};
+  int *d_tab = nullptr;
+  void *recF = nullptr, *recB = nullptr;  // FP64 (F64 mode) or FP32 (refined) records
+  int rsf = 8;                            // values per forward record
+  double *arec64 = nullptr;               // refined mode: FP64 A for the outer residual
   double *b64 = nullptr, *x64 = nullptr, *y64 = nullptr;
   float *r32 = nullptr, *d32 = nullptr, *y32 = nullptr;
   uint64_t *faces = nullptr;
@@ -107,6 +123,11 @@ struct sip_plan {
   std::vector<cudaEvent_t> pool;
   double prof_ms[K_NKINDS + 1] = {};
   long long prof_n[K_NKINDS + 1] = {};
+  // diagnostics: with SIP_TRACE=<file> in the environment every sweep launch
+  // records per-tile timestamps; the last launch of each kind is written to
+  // <file> when the plan is destroyed
+  unsigned long long *trace = nullptr;
+  std::string trace_path;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -122,6 +143,15 @@ cudaError_t palloc(sip_plan *p, T **ptr, size_t count) {
   p->bytes += b;
   *ptr = (T *)v;
   return cudaSuccess;
+}
+
+void pfree(sip_plan *p, void *v, size_t bytes) {
+  auto it = std::find(p->allocs.begin(), p->allocs.end(), v);
+  if (it != p->allocs.end()) {
+    p->allocs.erase(it);
+    p->bytes -= bytes;
+    cudaFree(v);
+  }
 }
 
 void free_plan_memory(sip_plan *p) {
@@ -140,109 +170,19 @@ void free_plan_memory(sip_plan *p) {
   p->h_status = nullptr;
 }
 
-// Plane layout of a block: plane s = i+j+k, rows k ascending, cells j
-// ascending; rbT[k*nplanes + s] + j is the cell's offset in the block.
-void build_rowbase(int nx, int ny, int nz, std::vector<int> &rbT) {
-  const int np = nx + ny + nz - 2;
-  rbT.assign((size_t)np * nz, INT_MIN);
-  long long off = 0;
-  for (int s = 0; s < np; ++s) {
-    const int klo = std::max(0, s - (nx - 1) - (ny - 1)), khi = std::min(nz - 1, s);
-    for (int k = klo; k <= khi; ++k) {
-      const int jlo = std::max(0, s - k - (nx - 1)), jhi = std::min(ny - 1, s - k);
-      if (jlo > jhi) continue;
-      rbT[(size_t)k * np + s] = (int)(off - jlo);
-      off += jhi - jlo + 1;
-    }
-  }
-}
-
-int tile_count(int ny, int nz, int TJ, int TK) { return ((ny + TJ - 1) / TJ) * ((nz + TK - 1) / TK); }
-
-}  // namespace
-
-// ------------------------------------------------------------------ ABI
-extern "C" {
-
-void sip_default_options(sip_options *opt) {
-  if (!opt) return;
-  std::memset(opt, 0, sizeof(*opt));
-  opt->alpha = 0.92;
-  opt->mode = SIP_MODE_F64;
-  opt->inner_iters = 4;
-  opt->max_spin = 0;
-}
-
-int sip_create(sip_ctx **out, int device, void *stream) {
-  if (!out) return SIP_ERR_INVALID_ARG;
-  *out = nullptr;
-  int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
-    g_create_error = "no CUDA device";
-    return SIP_ERR_NO_DEVICE;
-  }
-  if (device < 0 || device >= ndev) return SIP_ERR_INVALID_ARG;
-  if (cudaSetDevice(device) != cudaSuccess) return SIP_ERR_NO_DEVICE;
-  sip_ctx *ctx = new sip_ctx();
-  ctx->device = device;
-  ctx->stream = (cudaStream_t)stream;
-  cudaDeviceProp prop;
-  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
-    delete ctx;
-    return SIP_ERR_NO_DEVICE;
-  }
-  ctx->nsm = prop.multiProcessorCount;
-  ctx->smem_optin = prop.sharedMemPerBlockOptin;
-  for (int kind = 0; kind < K_NKINDS; ++kind)
-    for (int R : {3, 6}) {
-      const void *f = kernel_ptr(kind, R);
-      if (!f) continue;
-      cudaFuncAttributes fa;
-      cudaError_t e = cudaFuncGetAttributes(&fa, f);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(ctx->smem_optin - fa.sharedSizeBytes));
-      if (e != cudaSuccess) {
-        g_create_error = std::string("kernel attribute setup: ") + cudaGetErrorString(e);
-        delete ctx;
-        return SIP_ERR_CUDA;
-      }
-      ctx->kernel_static_smem = std::max(ctx->kernel_static_smem, (size_t)fa.sharedSizeBytes);
-    }
-  ctx->attrs_set = true;
-  *out = ctx;
-  return SIP_OK;
-}
-
-int sip_destroy(sip_ctx *ctx) {
-  delete ctx;
-  return SIP_OK;
-}
-
-const char *sip_last_error(sip_ctx *ctx) {
-  static thread_local std::string copy;
-  copy = ctx ? ctx->err : g_create_error;
-  return copy.c_str();
-}
-
-}  // extern "C"
-
-// ------------------------------------------------------------------ launches
-namespace {
-
-int max_active(sip_plan *p, int kind, int R, size_t smem) {
+int max_active(const void *f, int NT, size_t smem) {
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel_ptr(kind, R), p->NT, smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, NT, smem) != cudaSuccess) return 0;
   return occ;
 }
 
-SweepCommon common(sip_plan *p, bool backward, int ticket, int reset, int slot) {
+SweepCommon common(sip_plan *p, bool backward, int ticket, int reset, int slot, int kind) {
   SweepCommon c;
+  c.trace = p->trace ? p->trace + (size_t)kind * p->ntiles * kTraceWords : nullptr;
   c.blocks = p->d_blocks;
   c.tiles = backward ? p->d_tiles_b : p->d_tiles_f;
   c.ntiles = p->ntiles;
-  c.exch_cells = p->EC;
-  c.face_slots = p->FS;
+  c.tab_ints = p->tab_ints;
   c.ticket = p->tickets + ticket;
   c.reset_ticket = reset >= 0 ? p->tickets + reset : nullptr;
   c.ctl = p->ctl;
@@ -289,18 +229,18 @@ struct ProfScope {
 template <typename Params>
 cudaError_t launch(sip_plan *p, int kind, const Params &prm) {
   const int R = p->Rk[kind];
-  const size_t smem = kernel_smem(kind, R, p->NT, p->EC, p->FS);
+  const size_t smem = kernel_smem(kind, p->Q, R, p->NT, p->tab_ints);
   const int grid = std::max(1, std::min(p->ntiles, p->gridk[kind]));
   void *args[] = {(void *)&prm};
   ProfScope ps(p, kind);
-  return cudaLaunchKernel(kernel_ptr(kind, R), dim3(grid), dim3(p->NT), args, smem, p->ctx->stream);
+  return cudaLaunchKernel(kernel_ptr(kind, p->Q, R), dim3(grid), dim3(p->NT), args, smem, p->ctx->stream);
 }
 
 // utility launches (layout, reductions, control) are counted as kind K_NKINDS
-#define UTIL(call) \
-  do {             \
+#define UTIL(call)              \
+  do {                          \
     ProfScope ps_(p, K_NKINDS); \
-    CU(call);      \
+    CU(call);                   \
   } while (0)
 
 int check_status(sip_plan *p) {
@@ -320,17 +260,21 @@ int check_status(sip_plan *p) {
 int enqueue_iter_f64(sip_plan *p) {
   sip_ctx *ctx = p->ctx;
   FwdParams<double> f;
-  f.c = common(p, false, 0, 1, 0);
-  f.ap = p->A64[0]; f.aw = p->A64[1]; f.ae = p->A64[2]; f.as = p->A64[3];
-  f.an = p->A64[4]; f.ab = p->A64[5]; f.at = p->A64[6];
-  f.lb = p->F64[0]; f.lw = p->F64[1]; f.ls = p->F64[2]; f.rlp = p->F64[3];
-  f.b = p->b64; f.x = p->x64; f.y = p->y64; f.partials = p->partials;
+  f.c = common(p, false, 0, 1, 0, p->sym ? K_FWD64S : K_FWD64);
+  f.rec = (const double *)p->recF;
+  f.rsf = p->rsf;
+  f.b = p->b64;
+  f.x = p->x64;
+  f.y = p->y64;
+  f.partials = p->partials;
   CU(launch(p, p->sym ? K_FWD64S : K_FWD64, f));
   UTIL(launch_finalize(p->partials, p->ntiles, p->ctl, p->hist, p->hist_cap, p->status, FIN_RELRES, ctx->stream));
   BwdParams<double> b;
-  b.c = common(p, true, 1, 0, 1);
-  b.ue = p->F64[5]; b.un = p->F64[4]; b.ut = p->F64[6];
-  b.y = p->y64; b.x = p->x64; b.x64 = nullptr;
+  b.c = common(p, true, 1, 0, 1, K_BWD64);
+  b.rec = (const double *)p->recB;
+  b.y = p->y64;
+  b.x = p->x64;
+  b.x64 = nullptr;
   CU(launch(p, K_BWD64, b));
   return SIP_OK;
 }
@@ -340,21 +284,20 @@ int enqueue_iter_f64(sip_plan *p) {
 int enqueue_iter_refined(sip_plan *p) {
   sip_ctx *ctx = p->ctx;
   const int m = std::max(1, p->opt.inner_iters);
-  const bool a32 = (p->A64[0] == nullptr);
-  if (a32) {
+  if (p->a32in) {
     ResParams<float> r;
-    r.blocks = p->d_blocks; r.tiles = p->d_tiles_f; r.ntiles = p->ntiles; r.exch_cells = p->EC;
+    r.blocks = p->d_blocks; r.tiles = p->d_tiles_f; r.ntiles = p->ntiles; r.tab_ints = p->tab_ints;
     r.ctl = p->ctl; r.status = p->status;
-    r.ap = p->A32[0]; r.aw = p->A32[1]; r.ae = p->A32[2]; r.as = p->A32[3];
-    r.an = p->A32[4]; r.ab = p->A32[5]; r.at = p->A32[6];
+    r.arec = (const float *)p->recF + 4;
+    r.astride = p->rsf;
     r.b = p->b64; r.x = p->x64; r.r32 = p->r32; r.partials = p->partials;
     CU(launch(p, p->sym ? K_RES32AS : K_RES32A, r));
   } else {
     ResParams<double> r;
-    r.blocks = p->d_blocks; r.tiles = p->d_tiles_f; r.ntiles = p->ntiles; r.exch_cells = p->EC;
+    r.blocks = p->d_blocks; r.tiles = p->d_tiles_f; r.ntiles = p->ntiles; r.tab_ints = p->tab_ints;
     r.ctl = p->ctl; r.status = p->status;
-    r.ap = p->A64[0]; r.aw = p->A64[1]; r.ae = p->A64[2]; r.as = p->A64[3];
-    r.an = p->A64[4]; r.ab = p->A64[5]; r.at = p->A64[6];
+    r.arec = p->arec64;
+    r.astride = p->sym ? 4 : 8;
     r.b = p->b64; r.x = p->x64; r.r32 = p->r32; r.partials = p->partials;
     CU(launch(p, p->sym ? K_RES64S : K_RES64, r));
   }
@@ -362,18 +305,17 @@ int enqueue_iter_refined(sip_plan *p) {
   for (int q = 0; q < m; ++q) {
     const bool first = q == 0, lastq = q == m - 1;
     FwdParams<float> f;
-    f.c = common(p, false, 0, 1, 0);
-    f.ap = p->A32[0]; f.aw = p->A32[1]; f.ae = p->A32[2]; f.as = p->A32[3];
-    f.an = p->A32[4]; f.ab = p->A32[5]; f.at = p->A32[6];
-    f.lb = p->F32[0]; f.lw = p->F32[1]; f.ls = p->F32[2]; f.rlp = p->F32[3];
-    f.b = p->r32; f.x = p->d32; f.y = p->y32; f.partials = nullptr;
     const int fk = first ? K_FWD32Z : (p->sym ? K_FWD32S : K_FWD32);
+    f.c = common(p, false, 0, 1, 0, fk);
+    f.rec = (const float *)p->recF;
+    f.rsf = p->rsf;
+    f.b = p->r32; f.x = p->d32; f.y = p->y32; f.partials = nullptr;
     CU(launch(p, fk, f));
     BwdParams<float> b;
-    b.c = common(p, true, 1, 0, 1);
-    b.ue = p->F32[5]; b.un = p->F32[4]; b.ut = p->F32[6];
-    b.y = p->y32; b.x = p->d32; b.x64 = lastq ? p->x64 : nullptr;
     const int bk = first ? (lastq ? K_BWD32ZU : K_BWD32Z) : (lastq ? K_BWD32U : K_BWD32);
+    b.c = common(p, true, 1, 0, 1, bk);
+    b.rec = (const float *)p->recB;
+    b.y = p->y32; b.x = p->d32; b.x64 = lastq ? p->x64 : nullptr;
     CU(launch(p, bk, b));
   }
   return SIP_OK;
@@ -389,8 +331,8 @@ int begin_sequence(sip_plan *p, double rtol, int max_iters) {
   CU(cudaMemsetAsync(p->tickets, 0, 4 * sizeof(int), ctx->stream));
   UTIL(launch_set_ctl(p->ctl, rtol, max_iters, ctx->stream));
   for (auto &bh : p->blocks) {
-    UTIL(launch_to_plan_f64(bh.d.b, 0, p->b64, bh.db, 0, 0, ctx->stream));
-    UTIL(launch_to_plan_f64(bh.d.x, 0, p->x64, bh.db, 0, 0, ctx->stream));
+    UTIL(launch_to_plan_f64(bh.d.b, p->b64, bh.db, ctx->stream));
+    UTIL(launch_to_plan_f64(bh.d.x, p->x64, bh.db, ctx->stream));
   }
   UTIL(launch_sumsq_partials(p->b64, p->ncells, p->bparts, p->nbparts, ctx->stream));
   UTIL(launch_finalize(p->bparts, p->nbparts, p->ctl, p->hist, p->hist_cap, p->status, FIN_BNORM, ctx->stream));
@@ -407,9 +349,132 @@ int end_sequence(sip_plan *p) {
   return SIP_OK;
 }
 
+// kernels a plan of the given mode launches
+std::vector<int> plan_kinds(int mode, bool sym, bool a32in) {
+  if (mode == SIP_MODE_F64) return {K_FACTOR, sym ? K_FWD64S : K_FWD64, K_BWD64};
+  std::vector<int> k = {K_FACTOR32, K_FWD32Z, sym ? K_FWD32S : K_FWD32, K_BWD32, K_BWD32Z, K_BWD32U, K_BWD32ZU};
+  k.push_back(a32in ? (sym ? K_RES32AS : K_RES32A) : (sym ? K_RES64S : K_RES64));
+  return k;
+}
+
+// Tile shape: rows per thread Q and warps NW (tile = 32 x Q*NW).  Prefer the
+// shape whose tiles all fit on the GPU at once (one wave) and keep the most
+// SMs busy, then the fewest tile-to-tile hops; for every kernel the deepest
+// stage ring (6, else 4) that keeps the plan in one wave.
+struct ShapeChoice {
+  int Q = 0, NW = 0, ntiles = 0;
+  int R[K_NKINDS] = {}, cap[K_NKINDS] = {};
+  double score = -1e30;
+};
+
+ShapeChoice choose_shape(sip_ctx *ctx, const std::vector<BlockHost> &blocks, const std::vector<int> &kinds,
+                         int tab_ints, int forceTK, int forceR) {
+  ShapeChoice best;
+  for (int Q : kQs)
+    for (int NW = 1; NW <= 16; ++NW) {
+      const int TK = Q * NW, NT = 32 * NW;
+      if (forceTK > 0 && TK != forceTK) continue;
+      int ntiles = 0, hops = 0;
+      for (auto &bh : blocks) {
+        const int a = (bh.d.ny + kTJ - 1) / kTJ, b = (bh.d.nz + TK - 1) / TK;
+        ntiles += a * b;
+        hops = std::max(hops, a + b);
+      }
+      ShapeChoice c;
+      c.Q = Q;
+      c.NW = NW;
+      c.ntiles = ntiles;
+      bool ok = true;
+      int capmin = INT_MAX;
+      for (int kind : kinds) {
+        int bR = 0, bcap = 0;
+        for (int R : {6, 4}) {
+          if (forceR > 0 && R != forceR) continue;
+          const size_t smem = kernel_smem(kind, Q, R, NT, tab_ints);
+          if (smem + ctx->kernel_static_smem > ctx->smem_optin) continue;
+          const int capk = ctx->nsm * max_active(kernel_ptr(kind, Q, R), NT, smem);
+          if (capk >= ntiles) { bR = R; bcap = capk; break; }
+          if (capk > bcap) { bR = R; bcap = capk; }
+        }
+        if (bcap < 1) { ok = false; break; }
+        c.R[kind] = bR;
+        c.cap[kind] = bcap;
+        if (kernel_is_ticketed(kind)) capmin = std::min(capmin, bcap);
+      }
+      if (!ok) continue;
+      const bool onewave = capmin >= ntiles;
+      const double cover = (double)std::min(ntiles, ctx->nsm) / ctx->nsm;
+      c.score = (onewave ? 10.0 : 0.0) + cover - 0.002 * hops - (Q == 4 ? 0.0005 : 0.0);
+      if (c.score > best.score) best = c;
+    }
+  return best;
+}
+
 }  // namespace
 
+// ------------------------------------------------------------------ ABI
 extern "C" {
+
+void sip_default_options(sip_options *opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->alpha = 0.92;
+  opt->mode = SIP_MODE_F64;
+  opt->inner_iters = 4;
+  opt->max_spin = 0;
+}
+
+int sip_create(sip_ctx **out, int device, void *stream) {
+  if (!out) return SIP_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    g_create_error = "no CUDA device";
+    return SIP_ERR_NO_DEVICE;
+  }
+  if (device < 0 || device >= ndev) return SIP_ERR_INVALID_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return SIP_ERR_NO_DEVICE;
+  sip_ctx *ctx = new sip_ctx();
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)stream;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    delete ctx;
+    return SIP_ERR_NO_DEVICE;
+  }
+  ctx->nsm = prop.multiProcessorCount;
+  ctx->smem_optin = prop.sharedMemPerBlockOptin;
+  for (int kind = 0; kind < K_NKINDS; ++kind)
+    for (int Q : kQs)
+      for (int R : kRs) {
+        const void *f = kernel_ptr(kind, Q, R);
+        if (!f) continue;
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, f);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(ctx->smem_optin - fa.sharedSizeBytes));
+        if (e != cudaSuccess) {
+          g_create_error = std::string("kernel attribute setup: ") + cudaGetErrorString(e);
+          delete ctx;
+          return SIP_ERR_CUDA;
+        }
+        ctx->kernel_static_smem = std::max(ctx->kernel_static_smem, (size_t)fa.sharedSizeBytes);
+      }
+  *out = ctx;
+  return SIP_OK;
+}
+
+int sip_destroy(sip_ctx *ctx) {
+  delete ctx;
+  return SIP_OK;
+}
+
+const char *sip_last_error(sip_ctx *ctx) {
+  static thread_local std::string copy;
+  copy = ctx ? ctx->err : g_create_error;
+  return copy.c_str();
+}
 
 int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const sip_interface *ifaces,
                int nifaces, const sip_options *opt_in, sip_plan **out) {
@@ -421,8 +486,7 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
   sip_options opt;
   if (opt_in) opt = *opt_in;
   else sip_default_options(&opt);
-  if (!(opt.alpha >= 0.0 && opt.alpha <= 1.0))
-    return fail(ctx, SIP_ERR_INVALID_ARG, "alpha must lie in [0, 1]");
+  if (!(opt.alpha >= 0.0 && opt.alpha <= 1.0)) return fail(ctx, SIP_ERR_INVALID_ARG, "alpha must lie in [0, 1]");
   if (opt.mode != SIP_MODE_F64 && opt.mode != SIP_MODE_F32_REFINED)
     return fail(ctx, SIP_ERR_INVALID_ARG, "unsupported mode");
   if (opt.mode == SIP_MODE_F32_REFINED && opt.inner_iters < 1)
@@ -433,7 +497,7 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     const sip_block_desc &d = blocks[b];
     if (d.nx < 1 || d.ny < 1 || d.nz < 1) return fail(ctx, SIP_ERR_INVALID_ARG, "block dims must be >= 1");
     const long long n = (long long)d.nx * d.ny * d.nz;
-    if (n >= (1ll << 31) || (long long)d.nx + d.ny + d.nz > (1 << 24))
+    if (n >= (1ll << 31) || (long long)d.nx + d.ny + d.nz > (1 << 20))
       return fail(ctx, SIP_ERR_INVALID_ARG, "block too large (nx*ny*nz must be < 2^31)");
     if (d.coef_dtype != 0 && d.coef_dtype != 1) return fail(ctx, SIP_ERR_INVALID_ARG, "coef_dtype must be 0 or 1");
     if (!d.ap || !d.ae || !d.an || !d.at || !d.b || !d.x)
@@ -446,68 +510,70 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     ncells += n;
   }
   if (ncells >= (1ll << 31)) return fail(ctx, SIP_ERR_INVALID_ARG, "plan too large (total cells must be < 2^31)");
+  if (opt.tile_j != 0 && opt.tile_j != kTJ) return fail(ctx, SIP_ERR_INVALID_ARG, "tile_j must be 0 or 32");
+  if (opt.tile_k < 0 || opt.tile_k > 64 || (opt.tile_k > 0 && opt.tile_k % 2 != 0))
+    return fail(ctx, SIP_ERR_INVALID_ARG, "tile_k must be 0 (auto) or an even number <= 64");
+  if (opt.stages != 0 && opt.stages != 4 && opt.stages != 6)
+    return fail(ctx, SIP_ERR_INVALID_ARG, "stages must be 0 (auto), 4 or 6");
 
   sip_plan *p = new sip_plan();
   p->ctx = ctx;
   p->opt = opt;
   p->mode = opt.mode;
   p->sym = sym;
+  p->a32in = blocks[0].coef_dtype == 1;
   p->ncells = ncells;
-
-  // tile shape: threads per CTA and stage depth shared by every block
-  TileShape ts;
-  {
-    const int NT = 256;
-    int TJ = opt.tile_j, TK = opt.tile_k;
-    if (TJ <= 0 || TK <= 0) {
-      int maxny = 0;
-      for (int b = 0; b < nblocks; ++b) maxny = std::max(maxny, blocks[b].ny);
-      TJ = maxny >= 24 ? 32 : (maxny >= 12 ? 16 : 8);
-      TK = NT / TJ;
-    }
-    if (!(TJ == 8 || TJ == 16 || TJ == 32) || TK < 2 || TJ * TK > 512 || (TJ * TK) % 32 != 0) {
-      delete p;
-      return fail(ctx, SIP_ERR_INVALID_ARG, "tile_j must be 8, 16 or 32; tile_k >= 2; tile_j*tile_k a multiple of 32, <= 512");
-    }
-    ts.TJ = TJ;
-    ts.TK = TK;
-  }
-  p->NT = ts.TJ * ts.TK;
-  p->EC = (ts.TJ + 2) * (ts.TK + 2);
-  p->FS = ts.TJ + ts.TK;
-
-  // per-block layout tables and tile lists
-  std::vector<DevBlock> hdb;
-  std::vector<Tile> tiles;
-  long long cell0 = 0, face0 = 0;
-  size_t rb_total = 0;
   p->blocks.resize(nblocks);
   for (int b = 0; b < nblocks; ++b) {
     BlockHost &bh = p->blocks[b];
     bh.d = blocks[b];
-    const int nx = bh.d.nx, ny = bh.d.ny, nz = bh.d.nz;
-    build_rowbase(nx, ny, nz, bh.rbT);
-    bh.n = (long long)nx * ny * nz;
+    build_tables(bh.d.nx, bh.d.ny, bh.d.nz, bh.PO, bh.F);
+    bh.n = (long long)bh.d.nx * bh.d.ny * bh.d.nz;
+    p->tab_ints = std::max(p->tab_ints, (int)(bh.PO.size() + bh.F.size()));
+  }
+  const std::vector<int> kinds = plan_kinds(p->mode, sym, p->a32in);
+  const ShapeChoice sc = choose_shape(ctx, p->blocks, kinds, p->tab_ints, opt.tile_k, opt.stages);
+  if (sc.Q == 0) {
+    delete p;
+    return fail(ctx, SIP_ERR_INVALID_ARG, "no tile shape fits on an SM");
+  }
+  p->Q = sc.Q;
+  p->NW = sc.NW;
+  p->NT = 32 * sc.NW;
+  p->TK = sc.Q * sc.NW;
+  for (int k : kinds) {
+    p->Rk[k] = sc.R[k];
+    p->gridk[k] = sc.cap[k];
+  }
+
+  // per-block layout and tiles; claim order: anti-diagonal waves (cj + ck), blocks interleaved
+  std::vector<DevBlock> hdb;
+  std::vector<Tile> tiles;
+  long long cell0 = 0, face0 = 0;
+  size_t tab_total = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    BlockHost &bh = p->blocks[b];
     DevBlock &db = bh.db;
-    db.nx = nx; db.ny = ny; db.nz = nz; db.nplanes = nx + ny + nz - 2;
-    db.TJ = ts.TJ; db.TK = ts.TK;
-    db.nTJ = (ny + ts.TJ - 1) / ts.TJ;
-    db.nTK = (nz + ts.TK - 1) / ts.TK;
+    db.nx = bh.d.nx; db.ny = bh.d.ny; db.nz = bh.d.nz;
+    db.nplanes = db.nx + db.ny + db.nz - 2;
+    db.TK = p->TK;
+    db.nTJ = (db.ny + kTJ - 1) / kTJ;
+    db.nTK = (db.nz + p->TK - 1) / p->TK;
+    db.mmax = db.nx + db.ny - 2;
     db.tile0 = p->ntiles;
-    db.nsteps_max = nx + ts.TJ + ts.TK - 2;
+    db.nsteps_max = db.nx + kTJ + p->TK - 2;
     db.cell0 = cell0;
-    db.rbT = nullptr;
+    db.PO = db.F = nullptr;
     db.face0 = face0;
-    db.face_tile_words = (long long)db.nsteps_max * (ts.TJ + ts.TK) * kFaceWordsMax;
+    db.face_tile_words = (long long)db.nsteps_max * (kTJ + p->TK) * kFaceWordsMax;
     db.lo_blk = db.hi_blk = -1;
     db.lo_nj = db.lo_nk = db.hi_nj = db.hi_nk = 0;
     const int nt = db.nTJ * db.nTK;
     p->ntiles += nt;
     face0 += (long long)nt * db.face_tile_words;
     cell0 += bh.n;
-    rb_total += bh.rbT.size();
+    tab_total += bh.PO.size() + bh.F.size();
   }
-  // claim order: anti-diagonal waves (cj + ck), blocks interleaved
   {
     int maxwave = 0;
     for (auto &bh : p->blocks) maxwave = std::max(maxwave, bh.db.nTJ + bh.db.nTK - 2);
@@ -523,20 +589,21 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
   }
   std::vector<Tile> tiles_b(tiles.rbegin(), tiles.rend());
 
-  // device allocations
   auto bail = [&](cudaError_t e, const char *what) {
     free_plan_memory(p);
     delete p;
     return fail(ctx, e == cudaErrorMemoryAllocation ? SIP_ERR_OOM : SIP_ERR_CUDA,
                 std::string(what) + ": " + cudaGetErrorString(e));
   };
-#define PA(ptr, count)                                     \
-  do {                                                     \
-    cudaError_t e_ = palloc(p, &(ptr), (size_t)(count));   \
-    if (e_ != cudaSuccess) return bail(e_, #ptr);          \
+#define PA(ptr, count)                                   \
+  do {                                                   \
+    cudaError_t e_ = palloc(p, &(ptr), (size_t)(count)); \
+    if (e_ != cudaSuccess) return bail(e_, #ptr);        \
   } while (0)
   const long long N = ncells;
-  PA(p->d_rb, rb_total);
+  const bool f64 = p->mode == SIP_MODE_F64;
+  p->rsf = fwd_rec_values(sym);
+  PA(p->d_tab, tab_total);
   PA(p->d_blocks, nblocks);
   PA(p->d_tiles_f, p->ntiles);
   PA(p->d_tiles_b, p->ntiles);
@@ -548,25 +615,32 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
   PA(p->hist, p->hist_cap);
   PA(p->status, 1);
   PA(p->tickets, 4);
+  if (const char *tp = getenv("SIP_TRACE")) {
+    p->trace_path = tp;
+    PA(p->trace, (size_t)K_NKINDS * p->ntiles * kTraceWords);
+    cudaMemsetAsync(p->trace, 0, (size_t)K_NKINDS * p->ntiles * kTraceWords * 8, ctx->stream);
+  }
   PA(p->b64, N);
   PA(p->x64, N);
-  const bool a32in = blocks[0].coef_dtype == 1;
-  const int nA = 7;
-  // FP64 copy of A: sweeps of the FP64 mode, factorisation input always
-  double *A64tmp[7] = {};
-  for (int q = 0; q < nA; ++q) PA(A64tmp[q], N);
-  for (int q = 0; q < 7; ++q) PA(p->F64[q], N);
-  if (p->mode == SIP_MODE_F64) {
+  double *a7 = nullptr;
+  PA(a7, N * 8);
+  if (f64) {
+    double *rf = nullptr, *rb = nullptr;
+    PA(rf, N * p->rsf);
+    PA(rb, N * 4);
+    p->recF = rf;
+    p->recB = rb;
     PA(p->y64, N);
-    for (int q = 0; q < 7; ++q) p->A64[q] = A64tmp[q];
   } else {
+    float *rf = nullptr, *rb = nullptr;
+    PA(rf, N * p->rsf);
+    PA(rb, N * 4);
+    p->recF = rf;
+    p->recB = rb;
     PA(p->r32, N);
     PA(p->d32, N);
     PA(p->y32, N);
-    for (int q = 0; q < 7; ++q) PA(p->A32[q], N);
-    for (int q = 0; q < 7; ++q) PA(p->F32[q], N);
-    if (!a32in)
-      for (int q = 0; q < 7; ++q) p->A64[q] = A64tmp[q];
+    if (!p->a32in) PA(p->arec64, N * (sym ? 4 : 8));
   }
   {
     cudaError_t e = cudaMallocHost(&p->h_ctl, 3 * sizeof(Ctl));
@@ -574,18 +648,19 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     if (e != cudaSuccess) return bail(e, "pinned control block");
   }
   cudaStream_t st = ctx->stream;
-  // tables
   {
-    size_t off = 0;
+    std::vector<int> tab;
+    tab.reserve(tab_total);
     for (auto &bh : p->blocks) {
-      cudaError_t e = cudaMemcpyAsync(p->d_rb + off, bh.rbT.data(), bh.rbT.size() * sizeof(int),
-                                      cudaMemcpyHostToDevice, st);
-      if (e != cudaSuccess) return bail(e, "row tables");
-      bh.db.rbT = p->d_rb + off;
-      off += bh.rbT.size();
+      bh.db.PO = p->d_tab + tab.size();
+      tab.insert(tab.end(), bh.PO.begin(), bh.PO.end());
+      bh.db.F = p->d_tab + tab.size();
+      tab.insert(tab.end(), bh.F.begin(), bh.F.end());
       hdb.push_back(bh.db);
     }
-    cudaError_t e = cudaMemcpyAsync(p->d_blocks, hdb.data(), hdb.size() * sizeof(DevBlock), cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(p->d_tab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->d_blocks, hdb.data(), hdb.size() * sizeof(DevBlock), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(p->d_tiles_f, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
@@ -594,39 +669,30 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     if (e == cudaSuccess) e = cudaMemsetAsync(p->ctl, 0, sizeof(Ctl), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->tickets, 0, 4 * sizeof(int), st);
+    const size_t es = f64 ? 8 : 4;
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->recF, 0, (size_t)N * p->rsf * es, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->recB, 0, (size_t)N * 4 * es, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a7, 0, (size_t)N * 8 * sizeof(double), st);
+    if (e == cudaSuccess && p->arec64) e = cudaMemsetAsync(p->arec64, 0, (size_t)N * (sym ? 4 : 8) * 8, st);
     // host vectors must outlive the async copies
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bail(e, "plan upload");
   }
-  // Stage depth per kernel kind: the deepest ring (6, else 3) with which every
-  // tile of the plan is resident at once (one wave), else the one that keeps
-  // the most tiles resident.  The ticketed sweeps launch that many CTAs.
+  // A into the plan: the factorisation input (all seven entries, FP64), the
+  // sweep records' A part and, in the refined mode, the FP64 A of the outer
+  // residual.  Coefficients that point out of their block are zeroed.
   {
-    for (int kind = 0; kind < K_NKINDS; ++kind) {
-      int bestR = 0, bestCap = -1;
-      for (int R : {6, 3}) {
-        const size_t smem = kernel_smem(kind, R, p->NT, p->EC, p->FS);
-        if (smem + ctx->kernel_static_smem > ctx->smem_optin) continue;
-        const int cap = ctx->nsm * max_active(p, kind, R, smem);
-        if (cap >= p->ntiles) { bestR = R; bestCap = cap; break; }
-        if (cap > bestCap) { bestR = R; bestCap = cap; }
-      }
-      if (bestCap < 1) {
-        free_plan_memory(p);
-        delete p;
-        return fail(ctx, SIP_ERR_INVALID_ARG, "tile shape does not fit on an SM");
-      }
-      p->Rk[kind] = bestR;
-      p->gridk[kind] = bestCap;
-    }
-  }
-  // A into the plan layout; coefficients that point out of their block are zeroed
-  {
-    static const int zface[7] = {0, 1, 2, 3, 4, 5, 6};  // ap aw ae as an ab at
+    static const int zface[7] = {0, 1, 2, 3, 4, 5, 6};          // ap aw ae as an ab at
     static const int shift_src[7] = {-1, 2, -1, 4, -1, 6, -1};  // symmetric: aw<-ae, as<-an, ab<-at
     static const int shift_axis[7] = {0, 1, 0, 2, 0, 3, 0};
+    // slot of entry q in the forward record / the FP64 A record (-1: not stored)
+    const int fslot_s[7] = {RECS_AP, -1, RECS_AE, -1, RECS_AN, -1, RECS_AT};
+    const int fslot_g[7] = {RECG_AP, RECG_AW, RECG_AE, RECG_AS, RECG_AN, RECG_AB, RECG_AT};
+    const int aslot_s[7] = {0, -1, 1, -1, 2, -1, 3};
+    const int aslot_g[7] = {0, 1, 2, 3, 4, 5, 6};
     for (auto &bh : p->blocks) {
       const void *src[7] = {bh.d.ap, bh.d.aw, bh.d.ae, bh.d.as, bh.d.an, bh.d.ab, bh.d.at};
+      const int cd = bh.d.coef_dtype;
       for (int q = 0; q < 7; ++q) {
         const void *s = src[q];
         int sh = 0;
@@ -634,9 +700,13 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
           s = src[shift_src[q]];
           sh = shift_axis[q];
         }
-        cudaError_t e = launch_to_plan_f64(s, bh.d.coef_dtype, A64tmp[q], bh.db, sh ? 0 : zface[q], sh, st);
-        if (e == cudaSuccess && p->A32[0])
-          e = launch_to_plan_f32(s, bh.d.coef_dtype, p->A32[q], bh.db, sh ? 0 : zface[q], sh, st);
+        const int zf = sh ? 0 : zface[q];
+        cudaError_t e = launch_to_records(s, cd, a7, 0, 8, q, bh.db, zf, sh, st);
+        const int fs = sym ? fslot_s[q] : fslot_g[q];
+        if (e == cudaSuccess && fs >= 0) e = launch_to_records(s, cd, p->recF, f64 ? 0 : 1, p->rsf, fs, bh.db, zf, sh, st);
+        const int as = sym ? aslot_s[q] : aslot_g[q];
+        if (e == cudaSuccess && p->arec64 && as >= 0)
+          e = launch_to_records(s, cd, p->arec64, 0, sym ? 4 : 8, as, bh.db, zf, sh, st);
         if (e != cudaSuccess) return bail(e, "reorder A");
       }
     }
@@ -645,15 +715,25 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
   {
     cudaError_t e = launch_set_ctl(p->ctl, -1.0, 0, st);
     if (e != cudaSuccess) return bail(e, "control");
-    FacParams fp;
-    fp.c = common(p, false, 2, 0, 0);
-    for (int q = 0; q < 7; ++q) {
-      fp.a[q] = A64tmp[q];
-      fp.f[q] = p->F64[q];
-      fp.f32[q] = p->F32[q];
+    if (f64) {
+      FacParams<double> fp;
+      fp.c = common(p, false, 2, 0, 0, K_FACTOR);
+      fp.a7 = a7;
+      fp.recF = (double *)p->recF;
+      fp.recB = (double *)p->recB;
+      fp.rsf = p->rsf;
+      fp.alpha = opt.alpha;
+      e = launch(p, K_FACTOR, fp);
+    } else {
+      FacParams<float> fp;
+      fp.c = common(p, false, 2, 0, 0, K_FACTOR32);
+      fp.a7 = a7;
+      fp.recF = (float *)p->recF;
+      fp.recB = (float *)p->recB;
+      fp.rsf = p->rsf;
+      fp.alpha = opt.alpha;
+      e = launch(p, K_FACTOR32, fp);
     }
-    fp.alpha = opt.alpha;
-    e = launch(p, K_FACTOR, fp);
     if (e != cudaSuccess) return bail(e, "factor launch");
     int rc = check_status(p);
     if (rc != SIP_OK) {
@@ -662,6 +742,7 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
       delete p;
       return fail(ctx, rc, msg);
     }
+    pfree(p, a7, (size_t)N * 8 * sizeof(double));
   }
   *out = p;
   return SIP_OK;
@@ -696,7 +777,7 @@ int sip_solve(sip_plan *p, double rtol, int max_iters, int *iters_out, double *r
   cudaEvent_t ev[2];
   CU(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
   CU(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
-  int issued = 0;  // iterations queued (each starts with one residual + stop check)
+  int issued = 0;      // iterations queued (each starts with one residual + stop check)
   int nq = 0, nc = 0;  // chunks queued / checked
   bool more = true;
   for (;;) {
@@ -724,9 +805,9 @@ int sip_solve(sip_plan *p, double rtol, int max_iters, int *iters_out, double *r
   }
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
-  Ctl *hc = &p->h_ctl[2];
   rc = end_sequence(p);
   if (rc) return rc;
+  const Ctl *hc = &p->h_ctl[2];
   if (iters_out) *iters_out = hc->iter;
   if (relres_out) *relres_out = hc->relres;
   return hc->relres <= rtol ? SIP_OK : SIP_NOT_CONVERGED;
@@ -749,18 +830,23 @@ int sip_export_factors(sip_plan *p, int blk, double *const out[7]) {
   sip_ctx *ctx = p->ctx;
   for (int q = 0; q < 7; ++q)
     if (!out[q]) return fail(ctx, SIP_ERR_INVALID_ARG, "null output");
-  const double *f[7];
-  for (int q = 0; q < 7; ++q) f[q] = p->F64[q];
-  CU(launch_plan_to_natural_factors(f, out, p->blocks[blk].db, ctx->stream));
+  CU(launch_export_factors(p->recF, p->recB, p->mode == SIP_MODE_F64 ? 0 : 1, p->rsf, out, p->blocks[blk].db,
+                           ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
   return SIP_OK;
 }
 
 int sip_plane_layout(int nx, int ny, int nz, int32_t *rbT) {
   if (nx < 1 || ny < 1 || nz < 1 || !rbT || (long long)nx * ny * nz >= (1ll << 31)) return SIP_ERR_INVALID_ARG;
-  std::vector<int> t;
-  build_rowbase(nx, ny, nz, t);
-  std::memcpy(rbT, t.data(), t.size() * sizeof(int));
+  std::vector<int> PO, F;
+  build_tables(nx, ny, nz, PO, F);
+  const int np = nx + ny + nz - 2, mmax = nx + ny - 2;
+  for (int k = 0; k < nz; ++k)
+    for (int s = 0; s < np; ++s) {
+      const int m = s - k;
+      const bool row = m >= 0 && m <= mmax && std::max(0, m - (nx - 1)) <= std::min(ny - 1, m);
+      rbT[(size_t)k * np + s] = row ? plane_row_base(PO.data(), F.data(), mmax, nx, s, k) : INT32_MIN;
+    }
   return SIP_OK;
 }
 
@@ -806,7 +892,7 @@ const char *sip_kernel_name(int kind) {
   static const char *names[] = {"factor", "fwd64", "fwd64_sym", "bwd64", "fwd32", "fwd32_sym", "fwd32_x0",
                                 "fwd32_norm", "fwd32_sym_norm", "bwd32", "bwd32_x0", "bwd32_upd64",
                                 "bwd32_x0_upd64", "resid64", "resid64_sym", "resid64_a32", "resid64_a32_sym",
-                                "utility"};
+                                "factor32", "utility"};
   static_assert(sizeof(names) / sizeof(names[0]) == K_NKINDS + 1, "kernel names");
   if (kind < 0 || kind > K_NKINDS) return nullptr;
   return names[kind];
@@ -821,6 +907,26 @@ int sip_plan_bytes(sip_plan *p, size_t *bytes_out) {
 int sip_plan_destroy(sip_plan *p) {
   if (!p) return SIP_OK;
   cudaStreamSynchronize(p->ctx->stream);
+  if (p->trace && !p->trace_path.empty()) {
+    std::vector<unsigned long long> h((size_t)K_NKINDS * p->ntiles * kTraceWords);
+    if (cudaMemcpy(h.data(), p->trace, h.size() * 8, cudaMemcpyDeviceToHost) == cudaSuccess) {
+      FILE *fo = fopen(p->trace_path.c_str(), "a");
+      if (fo) {
+        fprintf(fo, "# plan ntiles=%d Q=%d NW=%d TK=%d\n", p->ntiles, p->Q, p->NW, p->TK);
+        for (int k = 0; k < K_NKINDS; ++k)
+          for (const auto &bh : p->blocks)
+            for (int ck = 0; ck < bh.db.nTK; ++ck)
+              for (int cj = 0; cj < bh.db.nTJ; ++cj) {
+                const int gt = bh.db.tile0 + ck * bh.db.nTJ + cj;
+                const unsigned long long *r = &h[((size_t)k * p->ntiles + gt) * kTraceWords];
+                if (!r[0]) continue;
+                fprintf(fo, "%s %d %d %d %llu %llu %llu %llu %llu %llu\n", sip_kernel_name(k), gt, cj, ck, r[0], r[1],
+                        r[2], r[3], r[4], r[5]);
+              }
+        fclose(fo);
+      }
+    }
+  }
   free_plan_memory(p);
   delete p;
   return SIP_OK;

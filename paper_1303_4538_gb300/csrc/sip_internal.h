@@ -11,27 +11,48 @@ constexpr int DEV_OK = 0;
 constexpr int DEV_TIMEOUT = 1;
 constexpr int DEV_BREAKDOWN = 2;
 
+constexpr int kTJ = 32;           // j extent of a column tile = one warp's lanes
+constexpr int kFaceWordsMax = 6;  // 3 FP64 values (the factorisation's UN, UE, UT)
+
+// Per-cell records of a plan (arrays of structs, 16-byte aligned):
+//   forward record  [LB LW LS 1/LP | AP AE AN AT]                   (symmetric, 8 values)
+//                   [LB LW LS 1/LP | AP AW AE AS AN AB AT 0]        (general, 12 values)
+//   backward record [UE UN UT 0]
+//   A record (FP64 residual of the refinement) [AP AE AN AT] or [AP AW AE AS AN AB AT 0]
+//   A7 record (factorisation input)            [AP AW AE AS AN AB AT 0]
+constexpr int REC_LB = 0, REC_LW = 1, REC_LS = 2, REC_RLP = 3;
+constexpr int RECS_AP = 4, RECS_AE = 5, RECS_AN = 6, RECS_AT = 7;  // symmetric forward record
+constexpr int RECG_AP = 4, RECG_AW = 5, RECG_AE = 6, RECG_AS = 7, RECG_AN = 8, RECG_AB = 9, RECG_AT = 10;
+constexpr int RECB_UE = 0, RECB_UN = 1, RECB_UT = 2;
+__host__ __device__ constexpr int fwd_rec_values(bool sym) { return sym ? 8 : 12; }
+
 // Plane layout of one block.  Plane s = i + j + k holds the cells with that
 // index sum; inside a plane the rows k ascend and inside a row the cells j
-// ascend, so cell (i, j, k) sits at cell0 + rbT[k * nplanes + s] + j.
-// Sweeps tile the (j, k) cross-section into TJ x TK column tiles; a CTA owns
-// one tile and walks it along i (one thread per (j, k) column).
+// ascend.  With f(m) the number of (i, j) with i + j = m and F(m) = sum of
+// f(0..m), cell (i, j, k) of plane s sits at
+//   cell0 + PO[s] + F[min(s, mmax)] - F[s - k] + j - max(0, s - k - (nx - 1)).
+// Sweeps tile the (j, k) cross-section into 32 x TK column tiles; a CTA owns
+// one tile and walks it along i (a warp owns Q rows k of the tile).
 struct DevBlock {
   int nx, ny, nz, nplanes;
-  int TJ, TK, nTJ, nTK;
+  int TK, nTJ, nTK, mmax;
   int tile0;            // global index of the block's tile (0, 0)
-  int nsteps_max;       // nx + TJ + TK - 2
+  int nsteps_max;       // nx + 32 + TK - 2
   long long cell0;      // first plan cell of the block
-  const int *rbT;       // row-base table, [nz][nplanes]
+  const int *PO;        // [nplanes] first cell of each plane
+  const int *F;         // [mmax + 1] prefix sums of the 2-D diagonal lengths
   long long face0;      // first face word of the block's tiles
-  long long face_tile_words;  // face words per tile (nsteps_max * (TJ + TK) * kFaceWordsMax)
+  long long face_tile_words;  // face words per tile (nsteps_max * (32 + TK) * kFaceWordsMax)
   // x-chain interfaces of a multi-block mesh: neighbour block across the -x
   // face (lo) and the +x face (hi), or -1; overlap rectangle j < nj, k < nk
   int lo_blk, hi_blk;
   int lo_nj, lo_nk, hi_nj, hi_nk;
 };
 
-constexpr int kFaceWordsMax = 6;  // 3 FP64 values (the factorisation's UN, UE, UT)
+__host__ __device__ inline int plane_row_base(const int *PO, const int *F, int mmax, int nx, int s, int k) {
+  const int m = s - k;
+  return PO[s] + F[s < mmax ? s : mmax] - F[m] - (m - nx + 1 > 0 ? m - nx + 1 : 0);
+}
 
 struct Tile {
   int blk;    // block index
@@ -56,8 +77,7 @@ struct SweepCommon {
   const DevBlock *blocks;
   const Tile *tiles;   // tiles in claim order
   int ntiles;
-  int exch_cells;      // max over blocks of (TJ + 2) * (TK + 2)
-  int face_slots;      // max over blocks of TJ + TK (consumer records staged per step)
+  int tab_ints;        // shared-memory capacity for one block's PO + F tables
   int *ticket;         // claim counter, zero at launch
   int *reset_ticket;   // counter this launch zeroes for the next launch (nullable)
   Ctl *ctl;            // epochs, done flag
@@ -66,13 +86,17 @@ struct SweepCommon {
   uint64_t *faces;
   int *status;
   long long max_spin;
+  // diagnostics (nullable): per tile [claim, gate passed, end, slow face waits,
+  // ns in slow waits, SM id]; globaltimer nanoseconds
+  unsigned long long *trace;
 };
+constexpr int kTraceWords = 6;
 
 template <typename T>
 struct FwdParams {
   SweepCommon c;
-  const T *ap, *aw, *ae, *as, *an, *ab, *at;  // plan layout (symmetric: aw, as, ab unused)
-  const T *lb, *lw, *ls, *rlp;
+  const T *rec;      // forward records
+  int rsf;           // values per forward record (8 symmetric, 12 general)
   const T *b, *x;
   T *y;
   double *partials;  // per global tile: sum of r^2
@@ -81,17 +105,19 @@ struct FwdParams {
 template <typename T>
 struct BwdParams {
   SweepCommon c;
-  const T *un, *ue, *ut;
+  const T *rec;  // backward records
   const T *y;
   T *x;          // correction accumulated in place (x <- x + d)
   double *x64;   // refined mode, last inner iteration: x64 += (double) x
 };
 
+template <typename TF>
 struct FacParams {
   SweepCommon c;
-  const double *a[7];  // ap aw ae as an ab at (plan layout)
-  double *f[7];        // lb lw ls rlp un ue ut
-  float *f32[7];       // optional single-precision copies (nullable)
+  const double *a7;  // A7 records
+  TF *recF;          // forward records (L part written)
+  TF *recB;          // backward records (U part written)
+  int rsf;           // values per forward record
   double alpha;
 };
 
@@ -100,29 +126,28 @@ struct ResParams {  // FP64 residual r = b - A x of the refinement loop (no recu
   const DevBlock *blocks;
   const Tile *tiles;
   int ntiles;
-  int exch_cells;
+  int tab_ints;
   Ctl *ctl;
   int *status;
-  const TA *ap, *aw, *ae, *as, *an, *ab, *at;
+  const TA *arec;   // A part of the records: [AP AE AN AT] or [AP AW AE AS AN AB AT 0]
+  int astride;      // values between consecutive cells' A parts
   const double *b, *x;
   float *r32;
   double *partials;
 };
 
 // utilities (sip_util.cu)
-cudaError_t launch_to_plan_f64(const void *src, int src_is_f32, double *dst, const DevBlock &hb,
-                               int zero_face, int shift_axis, cudaStream_t st);
-cudaError_t launch_to_plan_f32(const void *src, int src_is_f32, float *dst, const DevBlock &hb,
-                               int zero_face, int shift_axis, cudaStream_t st);
+cudaError_t launch_to_records(const void *src, int src_is_f32, void *dst, int dst_is_f32, int stride, int slot,
+                              const DevBlock &hb, int zero_face, int shift_axis, cudaStream_t st);
+cudaError_t launch_to_plan_f64(const double *src, double *dst, const DevBlock &hb, cudaStream_t st);
 cudaError_t launch_from_plan_f64(const double *src, double *dst, const DevBlock &hb, cudaStream_t st);
-cudaError_t launch_f64_to_f32(const double *src, float *dst, long long n, cudaStream_t st);
 cudaError_t launch_sumsq_partials(const double *v, long long n, double *partials, int nparts,
                                   cudaStream_t st);
 cudaError_t launch_finalize(const double *partials, int n, Ctl *ctl, double *hist, int hist_cap,
                             const int *status, int mode, cudaStream_t st);
 cudaError_t launch_set_ctl(Ctl *ctl, double rtol, int max_iters, cudaStream_t st);
-cudaError_t launch_plan_to_natural_factors(const double *const f[7], double *const out[7],
-                                           const DevBlock &hb, cudaStream_t st);
+cudaError_t launch_export_factors(const void *recF, const void *recB, int is_f32, int rsf,
+                                  double *const out[7], const DevBlock &hb, cudaStream_t st);
 
 // finalize modes
 constexpr int FIN_BNORM = 0;   // partials are ||b||^2 pieces: set ctl->bnorm

@@ -1,13 +1,13 @@
 // sip_kernels.h -- kernel registry of libsip.so: every sweep kernel variant is
-// addressed by (kind, stages) so the host runtime can size shared memory,
-// query occupancy and launch it with cudaLaunchKernel.
+// addressed by (kind, rows per thread Q, stages R) so the host runtime can size
+// shared memory, query occupancy and launch it with cudaLaunchKernel.
 #pragma once
 #include <cstddef>
 
 namespace sipk {
 
 enum KernelKind {
-  K_FACTOR = 0,   // Stone factorisation (FP64, optional FP32 copies)
+  K_FACTOR = 0,   // Stone factorisation, FP64 factors
   K_FWD64,        // FP64 residual + norm + forward substitution, general A
   K_FWD64S,       // same, symmetric A (Listing 1 residual)
   K_BWD64,        // FP64 backward substitution + update
@@ -24,16 +24,20 @@ enum KernelKind {
   K_RES64S,       // same, symmetric
   K_RES32A,       // FP64 residual, A stored in FP32 (widened)
   K_RES32AS,      // same, symmetric
+  K_FACTOR32,     // Stone factorisation (FP64 arithmetic), FP32 factors
   K_NKINDS
 };
 
-const void *kernel_ptr(int kind, int stages);
-// dynamic shared memory of a launch with `nthreads` threads per CTA, an
-// exchange area of `exch_cells` cells and `face_slots` staged face records
-size_t kernel_smem(int kind, int stages, int nthreads, int exch_cells, int face_slots);
+constexpr int kQs[2] = {2, 4};
+constexpr int kRs[2] = {4, 6};
+
+const void *kernel_ptr(int kind, int Q, int R);
+// dynamic shared memory of a launch with `nthreads` threads per CTA
+size_t kernel_smem(int kind, int Q, int R, int nthreads, int tab_ints);
 bool kernel_is_ticketed(int kind);
 
-const void *kernel_ptr_64(int kind, int stages);
-const void *kernel_ptr_32(int kind, int stages);
+const void *kernel_ptr_64(int kind, int Q, int R);
+const void *kernel_ptr_32(int kind, int Q, int R);
+const void *kernel_ptr_res(int kind, int Q, int R);
 
 }  // namespace sipk

@@ -6,28 +6,31 @@
 // T (backward substitution).  All cells of one hyperplane i + j + k = s are
 // independent, so the sweeps advance plane by plane.  Work decomposition:
 //
-//   * the (j, k) cross-section of a block is cut into TJ x TK column tiles;
-//     one CTA owns a tile, one thread owns a (j, k) column and walks i, so at
-//     local step t every thread of the tile is on global plane s = t + j0 + k0;
-//   * inside the tile the neighbour values of the previous (or next) plane
-//     pass through a double-buffered shared-memory exchange, one barrier per
-//     step; W/E come from the thread's own registers;
-//   * the cell data of each step (coefficients, factors, rhs, x) is staged
-//     by cp.async into a per-thread ring of R shared-memory stages, R-1 steps
-//     ahead of use; invalid cells are zero-filled, so the arithmetic runs
-//     without branches and inactive threads produce zeros;
+//   * the (j, k) cross-section of a block is cut into 32 x TK column tiles;
+//     one CTA owns a tile; lane = j, and warp w owns the Q rows
+//     k = k0 + w Q .. k0 + w Q + Q - 1, so a thread walks Q columns along i.
+//     At local step t every cell the CTA touches lies on plane s = t + j0 + k0;
+//   * neighbours of the previous (next) plane: W/E from the thread's own
+//     registers, S/N from lanes j -+ 1 by warp shuffles, B/T from the
+//     thread's own neighbouring row, and across warps through a
+//     double-buffered shared-memory exchange (one barrier per step);
+//   * each cell's static data (coefficients and factors) is one 16-byte
+//     aligned record, staged with cp.async.cg (L2 only) R-1 steps ahead into a
+//     ring of shared-memory stages together with the rhs and x values; invalid
+//     cells are zero-filled, so the arithmetic runs without branches and
+//     inactive threads produce zeros;
+//   * row addresses come from two small per-block tables held in shared
+//     memory (plane offsets PO and the diagonal prefix sums F);
 //   * between tiles, the recurrence's boundary values travel through "faces":
 //     16-byte records of two 8-byte words whose upper halves carry the
 //     launch's epoch tag.  A producer stores a record with one st.relaxed.gpu;
-//     a consumer prefetches it with cp.async.cg into a shared-memory ring
-//     together with the step's other data and accepts it when every tag
-//     matches (each word is self-validating, so no fence or flag is needed);
-//     a stale record is re-read from L2 with ld.relaxed.gpu until it matches.
-//     Before a tile starts, one thread waits until the upstream tiles are a
-//     few steps ahead ("slack"), so the prefetched records are normally valid
-//     and no step pays an L2 round trip.  Every wait is bounded (max_spin
-//     polls), then the kernel records DEV_TIMEOUT and runs to the end
-//     without waiting again;
+//     a consumer prefetches it with cp.async.cg with the step's other data and
+//     accepts it when every tag matches (each word is self-validating, so no
+//     fence or flag is needed); a stale record is re-read from L2 with
+//     ld.relaxed.gpu until it matches.  Before a tile starts, one thread waits
+//     until the upstream tiles are a few steps ahead ("slack"), so prefetched
+//     records are normally valid.  Every wait is bounded (max_spin polls),
+//     then the kernel records DEV_TIMEOUT and runs to the end without waiting;
 //   * CTAs claim tiles with an atomic ticket in a dependency-respecting order,
 //     so a tile only waits for tiles claimed earlier by running CTAs.
 #pragma once
@@ -35,6 +38,7 @@
 #include <cuda_runtime.h>
 
 #include "sip_internal.h"
+#include "sip_layout.h"
 
 namespace sipk {
 
@@ -49,8 +53,10 @@ __device__ __forceinline__ void cp_async_zfill(void *sdst, const void *gsrc, boo
                "n"(BYTES), "r"(valid ? BYTES : 0)
                : "memory");
 }
-__device__ __forceinline__ void cp_async_16_l2(void *sdst, const void *gsrc) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+__device__ __forceinline__ void cp_async_16_l2(void *sdst, const void *gsrc, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(sdst)), "l"(gsrc),
+               "r"(valid ? 16 : 0)
+               : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -70,6 +76,26 @@ __device__ __forceinline__ int ld_relaxed(const int *p) {
   int v;
   asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned smid() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_up1(T v) {
+  return __shfl_up_sync(0xffffffffu, v, 1);
+}
+template <typename T>
+__device__ __forceinline__ T shfl_dn1(T v) {
+  return __shfl_down_sync(0xffffffffu, v, 1);
 }
 
 // ---------------------------------------------------------------- faces
@@ -109,13 +135,20 @@ __device__ __forceinline__ bool rec_ok(const uint64_t (&w)[W], unsigned expect) 
 // error; `abort` then stays set so this thread never waits again.
 template <int W>
 __device__ __noinline__ bool face_wait(const uint64_t *p, unsigned expect, uint64_t (&w)[W],
-                                       const SweepCommon &c, bool &abort) {
+                                       const SweepCommon &c, bool &abort, unsigned long long *tr) {
   if (!abort) {
     long long spins = 0;
+    const unsigned long long t0 = tr ? gtimer() : 0ull;
     for (;;) {
 #pragma unroll
       for (int q = 0; q < W; ++q) w[q] = ld_relaxed(p + q);
-      if (rec_ok<W>(w, expect)) return true;
+      if (rec_ok<W>(w, expect)) {
+        if (tr) {
+          atomicAdd(tr + 3, 1ull);
+          atomicAdd(tr + 4, gtimer() - t0);
+        }
+        return true;
+      }
       ++spins;
       if (spins > c.max_spin) {
         atomicCAS(c.status, DEV_OK, DEV_TIMEOUT);
@@ -137,20 +170,21 @@ __device__ __noinline__ bool face_wait(const uint64_t *p, unsigned expect, uint6
 // Take the record staged in shared memory; re-read it from L2 if it is stale.
 template <int W>
 __device__ __forceinline__ void rec_take(const uint64_t *staged, const uint64_t *g, unsigned expect,
-                                         uint64_t (&w)[W], const SweepCommon &c, bool &abort) {
+                                         uint64_t (&w)[W], const SweepCommon &c, bool &abort,
+                                         unsigned long long *tr) {
 #pragma unroll
   for (int q = 0; q < W; ++q) w[q] = staged[q];
-  if (!rec_ok<W>(w, expect)) face_wait<W>(g, expect, w, c, abort);
+  if (!rec_ok<W>(w, expect)) face_wait<W>(g, expect, w, c, abort, tr);
 }
 
 template <int W>
 __device__ __forceinline__ void rec_prefetch(uint64_t *sdst, const uint64_t *g) {
 #pragma unroll
-  for (int q = 0; q < W; q += 2) cp_async_16_l2(sdst + q, g + q);
+  for (int q = 0; q < W; q += 2) cp_async_16_l2(sdst + q, g + q, true);
 }
 
 // Face storage of one tile: J face [nsteps_max][TK][W], then K face
-// [nsteps_max][TJ][W], indexed by the producer's local step.
+// [nsteps_max][32][W], indexed by the producer's local step.
 __device__ __forceinline__ uint64_t *tile_faces(const SweepCommon &c, const DevBlock &B, int gtile) {
   return c.faces + B.face0 + (long long)(gtile - B.tile0) * B.face_tile_words;
 }
@@ -158,7 +192,7 @@ __device__ __forceinline__ uint64_t *faceJ(uint64_t *base, const DevBlock &B, in
   return base + ((long long)t * B.TK + lane) * W;
 }
 __device__ __forceinline__ uint64_t *faceK(uint64_t *base, const DevBlock &B, int t, int lane, int W) {
-  return base + (long long)B.nsteps_max * B.TK * W + ((long long)t * B.TJ + lane) * W;
+  return base + (long long)B.nsteps_max * B.TK * W + ((long long)t * kTJ + lane) * W;
 }
 
 // Claim the next tile (thread 0), broadcast through shared memory.
@@ -198,42 +232,48 @@ __device__ __forceinline__ double block_sum(double v, double *s_red) {
   return t;
 }
 
-struct ColGeom {
-  int dj, dk, j0, k0, j, k, nsteps, s0, njt, nkt;
-  bool col, hasS, hasN, hasB, hasT;
-  __device__ ColGeom(const DevBlock &B, const Tile &tl) {
-    dj = threadIdx.x % B.TJ;
-    dk = threadIdx.x / B.TJ;
-    j0 = tl.cj * B.TJ;
-    k0 = tl.ck * B.TK;
-    j = j0 + dj;
-    k = k0 + dk;
-    col = (j < B.ny) && (k < B.nz) && (dk < B.TK);
-    njt = min(B.TJ, B.ny - j0);
-    nkt = min(B.TK, B.nz - k0);
+// Copy the block's PO and F tables into shared memory when the CTA moves to a
+// tile of another block (block-uniform: s_blk is read after a barrier).
+__device__ __forceinline__ void load_tables(const DevBlock &B, int blk, int *sPO, int *s_blk) {
+  if (*s_blk != blk) {
+    for (int q = threadIdx.x; q < B.nplanes; q += blockDim.x) sPO[q] = B.PO[q];
+    int *sF = sPO + B.nplanes;
+    for (int q = threadIdx.x; q <= B.mmax; q += blockDim.x) sF[q] = B.F[q];
+    __syncthreads();
+    if (threadIdx.x == 0) *s_blk = blk;
+  }
+}
+
+// Geometry of the calling thread inside tile (cj, ck): lane = j - j0,
+// warp w owns rows k0 + w Q + q.
+template <int Q>
+struct Geo {
+  int lane, w, NW, TK, j0, k0, j, s0, nsteps, njt, nkt;
+  bool jok, hasS, hasN, hasB, hasT, eB, eT;
+  __device__ Geo(const DevBlock &B, const Tile &tl) {
+    lane = threadIdx.x & 31;
+    w = threadIdx.x >> 5;
+    NW = blockDim.x >> 5;
+    TK = NW * Q;
+    j0 = tl.cj * kTJ;
+    k0 = tl.ck * TK;
+    j = j0 + lane;
+    jok = j < B.ny;
+    njt = min(kTJ, B.ny - j0);
+    nkt = min(TK, B.nz - k0);
     nsteps = B.nx + njt + nkt - 2;
     s0 = j0 + k0;
     hasS = j0 > 0;
-    hasN = j0 + B.TJ < B.ny;
+    hasN = j0 + kTJ < B.ny;
     hasB = k0 > 0;
-    hasT = k0 + B.TK < B.nz;
+    hasT = k0 + TK < B.nz;
+    eB = w == 0;
+    eT = w == NW - 1;
   }
-};
-
-// Shared-memory carve-up of a sweep kernel: stage ring, exchange buffer, face ring.
-template <typename T>
-struct Smem {
-  T *stage;       // [R][NV][NT]
-  T *exch;        // [2][NE][EC]
-  uint64_t *fst;  // [R][FS][W]
-  __device__ Smem(unsigned char *raw, int R, int NV, int NT, int NE, int EC) {
-    stage = reinterpret_cast<T *>(raw);
-    size_t off = (size_t)R * NV * NT * sizeof(T);
-    exch = reinterpret_cast<T *>(raw + off);
-    off += (size_t)2 * NE * EC * sizeof(T);
-    off = (off + 15) & ~(size_t)15;
-    fst = reinterpret_cast<uint64_t *>(raw + off);
-  }
+  __device__ int k(int q) const { return k0 + w * Q + q; }
+  __device__ int dk(int q) const { return w * Q + q; }
+  __device__ bool col(const DevBlock &B, int q) const { return jok && k(q) < B.nz; }
+  __device__ int i(int t, int q) const { return t - lane - dk(q); }
 };
 
 // Slack gate: before a tile starts, wait until the records that the tile will
@@ -241,14 +281,24 @@ struct Smem {
 // prefetched during the walk are normally already valid.
 template <int W>
 __device__ __forceinline__ void slack_gate(const uint64_t *recJ, const uint64_t *recK, unsigned expect,
-                                           const SweepCommon &c, bool &abort) {
+                                           const SweepCommon &c, bool &abort, unsigned long long *tr) {
   if (threadIdx.x == 0) {
     uint64_t w[W];
-    if (recJ) face_wait<W>(recJ, expect, w, c, abort);
-    if (recK) face_wait<W>(recK, expect, w, c, abort);
+    if (tr) {
+      tr[0] = gtimer();
+      tr[5] = smid();
+    }
+    if (recJ) face_wait<W>(recJ, expect, w, c, abort, nullptr);
+    if (recK) face_wait<W>(recK, expect, w, c, abort, nullptr);
+    if (tr) tr[1] = gtimer();
   }
   __syncthreads();
 }
+
+template <typename T, int N>
+struct Vec {
+  T v[N];
+};
 
 // ============================================================== factorisation
 // Stone's factorisation, per cell after W, S, B (lu3d):
@@ -257,20 +307,26 @@ __device__ __forceinline__ void slack_gate(const uint64_t *recJ, const uint64_t 
 //   P1 = a (LB UN_B + LW UN_W),  P2 = a (LB UE_B + LS UE_S),  P3 = a (LW UT_W + LS UT_S),
 //   LP = AP + P1 + P2 + P3 - LB UT_B - LW UE_W - LS UN_S,
 //   UN = (AN - P1) / LP,  UE = (AE - P2) / LP,  UT = (AT - P3) / LP.
-// Stored: LB, LW, LS, 1/LP, UN, UE, UT.  Faces carry (UN, UE, UT): 48 bytes.
-template <int R>
-__global__ void __launch_bounds__(512) k_factor(FacParams P) {
+// Arithmetic in FP64; stored (as TF) into the forward record [LB LW LS 1/LP]
+// and the backward record [UE UN UT 0].  Faces carry (UN, UE, UT): 48 bytes.
+template <typename TF, int Q, int R>
+__global__ void __launch_bounds__(512) k_factor(FacParams<TF> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_claim;
-  constexpr int NV = 7, W = 6;
+  __shared__ int s_claim, s_blk;
+  constexpr int W = 6;
   const SweepCommon &c = P.c;
   const unsigned ep = sweep_prologue(c);
+  if (threadIdx.x == 0) s_blk = -1;
   // block-uniform exit decision (the status word may change during the launch)
   if (__syncthreads_or(ld_relaxed(c.status) != DEV_OK)) return;
   const unsigned expect = ep + (c.stall ? 0x40000000u : 0u);
   const int NT = blockDim.x, tid = threadIdx.x;
-  const int EC = c.exch_cells, FS = c.face_slots;
-  Smem<double> sm(smem_raw, R, NV, NT, 3, EC);
+  const SweepLayout L = fac_layout(Q, R, NT, c.tab_ints);
+  int *sPO = reinterpret_cast<int *>(smem_raw);
+  unsigned char *stage = smem_raw + L.tab;
+  double *exB = reinterpret_cast<double *>(stage + (size_t)R * L.step);  // [2][3][NW][32]
+  uint64_t *fst = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(exB) + L.exch);
+  const int FS = L.fs;
   bool abort = false;
 
   for (;;) {
@@ -278,112 +334,159 @@ __global__ void __launch_bounds__(512) k_factor(FacParams P) {
     if (m >= c.ntiles) break;
     const Tile tl = c.tiles[m];
     const DevBlock B = c.blocks[tl.blk];
-    const ColGeom g(B, tl);
-    const int *rbk = B.rbT + (long long)min(g.k, B.nz - 1) * B.nplanes;
+    unsigned long long *tr = c.trace ? c.trace + (size_t)tl.gtile * kTraceWords : nullptr;
+    load_tables(B, tl.blk, sPO, &s_blk);
+    const int *sF = sPO + B.nplanes;
+    const Geo<Q> g(B, tl);
+    const int NW = g.NW, lane = g.lane, w = g.w;
     uint64_t *myf = tile_faces(c, B, tl.gtile);
     uint64_t *upJ = g.hasS ? tile_faces(c, B, tl.gtile - 1) : nullptr;
     uint64_t *upK = g.hasB ? tile_faces(c, B, tl.gtile - B.nTJ) : nullptr;
-    const int TJ2 = B.TJ + 2;
-    const int me = (g.dk + 1) * TJ2 + g.dj + 1;
-    const bool cJ = g.dj == 0 && g.hasS, cK = g.dk == 0 && g.hasB;  // face consumers
     {
       const int lead = min(R + 1, B.nx - 1);
-      slack_gate<W>(upJ ? faceJ(upJ, B, lead + B.TJ - 1, 0, W) : nullptr,
-                    upK ? faceK(upK, B, lead + B.TK - 1, 0, W) : nullptr, expect, c, abort);
+      slack_gate<W>(upJ ? faceJ(upJ, B, lead + kTJ - 1, 0, W) : nullptr,
+                    upK ? faceK(upK, B, lead + g.TK - 1, 0, W) : nullptr, expect, c, abort, tr);
     }
+    auto rb = [&](int s, int k) { return plane_row_base(sPO, sF, B.mmax, B.nx, s, k); };
 
     auto issue = [&](int tt) {
       if (tt < g.nsteps) {
-        const int i = tt - g.dj - g.dk;
-        const bool v = g.col && i >= 0 && i < B.nx;
-        const long long a = v ? B.cell0 + rbk[g.s0 + tt] + g.j : 0;
-        double *st = sm.stage + (size_t)(tt % R) * NV * NT + tid;
+        const int s = g.s0 + tt;
+        unsigned char *st = stage + (size_t)(tt % R) * L.step;
+        uint64_t *fs = fst + (size_t)(tt % R) * FS * W;
 #pragma unroll
-        for (int q = 0; q < NV; ++q) cp_async_zfill<8>(st + q * NT, P.a[q] + a, v);
-        uint64_t *fs = sm.fst + (size_t)(tt % R) * FS * W;
-        if (cJ && v) rec_prefetch<W>(fs + g.dk * W, faceJ(upJ, B, tt + B.TJ - 1, g.dk, W));
-        if (cK && v) rec_prefetch<W>(fs + (B.TK + g.dj) * W, faceK(upK, B, tt + B.TK - 1, g.dj, W));
+        for (int q = 0; q < Q; ++q) {
+          const int i = g.i(tt, q);
+          const bool v = g.col(B, q) && i >= 0 && i < B.nx;
+          const long long a = v ? B.cell0 + rb(s, g.k(q)) + g.j : 0;
+          unsigned char *d = st + ((size_t)q * NT + tid) * 64;
+          const unsigned char *src = reinterpret_cast<const unsigned char *>(P.a7 + a * 8);
+#pragma unroll
+          for (int z = 0; z < 4; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v);
+          if (lane == 0 && g.hasS && v) rec_prefetch<W>(fs + g.dk(q) * W, faceJ(upJ, B, tt + kTJ - 1, g.dk(q), W));
+          if (q == 0 && g.eB && g.hasB && v)
+            rec_prefetch<W>(fs + (g.TK + lane) * W, faceK(upK, B, tt + g.TK - 1, lane, W));
+        }
       }
       cp_async_commit();
     };
 #pragma unroll
     for (int tt = 0; tt < R - 1; ++tt) issue(tt);
 
-    double unW = 0, ueW = 0, utW = 0;
+    double unW[Q], ueW[Q], utW[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) unW[q] = ueW[q] = utW[q] = 0.0;
     const double al = P.alpha;
     for (int t = 0; t < g.nsteps; ++t) {
       issue(t + R - 1);
       cp_async_wait<R - 1>();
-      const double *st = sm.stage + (size_t)(t % R) * NV * NT + tid;
-      const uint64_t *fs = sm.fst + (size_t)(t % R) * FS * W;
-      const int i = t - g.dj - g.dk;
-      const bool act = g.col && i >= 0 && i < B.nx;
-      double *E = sm.exch + (size_t)(t & 1) * 3 * EC;
-      E[me] = unW;
-      E[EC + me] = ueW;
-      E[2 * EC + me] = utW;
-      if (g.dj == 0) {
-        uint64_t w[W] = {0, 0, 0, 0, 0, 0};
-        if (act && cJ) rec_take<W>(fs + g.dk * W, faceJ(upJ, B, t + B.TJ - 1, g.dk, W), expect, w, c, abort);
-        E[me - 1] = Face<double>::get(w);
-        E[EC + me - 1] = Face<double>::get(w + 2);
-        E[2 * EC + me - 1] = Face<double>::get(w + 4);
-      }
-      if (g.dk == 0) {
-        uint64_t w[W] = {0, 0, 0, 0, 0, 0};
-        if (act && cK)
-          rec_take<W>(fs + (B.TK + g.dj) * W, faceK(upK, B, t + B.TK - 1, g.dj, W), expect, w, c, abort);
-        E[me - TJ2] = Face<double>::get(w);
-        E[EC + me - TJ2] = Face<double>::get(w + 2);
-        E[2 * EC + me - TJ2] = Face<double>::get(w + 4);
+      const unsigned char *st = stage + (size_t)(t % R) * L.step;
+      const uint64_t *fs = fst + (size_t)(t % R) * FS * W;
+      const int buf = t & 1;
+      double *E = exB + (size_t)buf * 3 * NW * 32;
+      E[(0 * NW + w) * 32 + lane] = unW[Q - 1];
+      E[(1 * NW + w) * 32 + lane] = ueW[Q - 1];
+      E[(2 * NW + w) * 32 + lane] = utW[Q - 1];
+      double hK[3] = {0, 0, 0};
+      if (g.eB) {
+        const int i0 = g.i(t, 0);
+        if (g.hasB && g.col(B, 0) && i0 >= 0 && i0 < B.nx) {
+          uint64_t wv[W];
+          rec_take<W>(fs + (g.TK + lane) * W, faceK(upK, B, t + g.TK - 1, lane, W), expect, wv, c, abort, tr);
+          hK[0] = Face<double>::get(wv);
+          hK[1] = Face<double>::get(wv + 2);
+          hK[2] = Face<double>::get(wv + 4);
+        }
       }
       __syncthreads();
-      const double unS = E[me - 1], ueS = E[EC + me - 1], utS = E[2 * EC + me - 1];
-      const double unB = E[me - TJ2], ueB = E[EC + me - TJ2], utB = E[2 * EC + me - TJ2];
-      const double ap = st[0], aw = st[NT], ae = st[2 * NT], as = st[3 * NT], an = st[4 * NT],
-                   ab = st[5 * NT], at = st[6 * NT];
-      const double LB = ab / (1.0 + al * (unB + ueB));
-      const double LW = aw / (1.0 + al * (unW + utW));
-      const double LS = as / (1.0 + al * (ueS + utS));
-      const double P1 = al * (LB * unB + LW * unW);
-      const double P2 = al * (LB * ueB + LS * ueS);
-      const double P3 = al * (LW * utW + LS * utS);
-      const double LP = ap + P1 + P2 + P3 - LB * utB - LW * ueW - LS * unS;
-      double UN = 0, UE = 0, UT = 0;
-      if (act) {
-        UN = (an - P1) / LP;
-        UE = (ae - P2) / LP;
-        UT = (at - P3) / LP;
-        const double RLP = 1.0 / LP;
-        if (LP == 0.0 || !isfinite(RLP) || !isfinite(LB) || !isfinite(LW) || !isfinite(LS) ||
-            !isfinite(UN) || !isfinite(UE) || !isfinite(UT) || !isfinite(LP))
-          atomicCAS(c.status, DEV_OK, DEV_BREAKDOWN);
-        const long long a = B.cell0 + rbk[g.s0 + t] + g.j;
-        const double outv[7] = {LB, LW, LS, RLP, UN, UE, UT};
+      double nUN[Q], nUE[Q], nUT[Q];
 #pragma unroll
-        for (int q = 0; q < 7; ++q) P.f[q][a] = outv[q];
-        if (P.f32[0]) {
-#pragma unroll
-          for (int q = 0; q < 7; ++q) P.f32[q][a] = (float)outv[q];
+      for (int q = 0; q < Q; ++q) {
+        const int i = g.i(t, q);
+        const bool act = g.col(B, q) && i >= 0 && i < B.nx;
+        const double *a = reinterpret_cast<const double *>(st + ((size_t)q * NT + tid) * 64);
+        const double ap = a[0], aw = a[1], ae = a[2], as = a[3], an = a[4], ab = a[5], at = a[6];
+        // S neighbour (lane - 1, same row, previous step) or the J face
+        double unS = shfl_up1(unW[q]), ueS = shfl_up1(ueW[q]), utS = shfl_up1(utW[q]);
+        if (lane == 0) {
+          unS = ueS = utS = 0.0;
+          if (g.hasS && act) {
+            uint64_t wv[W];
+            rec_take<W>(fs + g.dk(q) * W, faceJ(upJ, B, t + kTJ - 1, g.dk(q), W), expect, wv, c, abort, tr);
+            unS = Face<double>::get(wv);
+            ueS = Face<double>::get(wv + 2);
+            utS = Face<double>::get(wv + 4);
+          }
         }
-        if (g.dj == B.TJ - 1 && g.hasN) {
-          uint64_t *f = faceJ(myf, B, t, g.dk, W);
-          Face<double>::put(f, UN, ep);
-          Face<double>::put(f + 2, UE, ep);
-          Face<double>::put(f + 4, UT, ep);
+        // B neighbour (row q - 1 of this thread, the previous warp, or the K face)
+        double unB, ueB, utB;
+        if (q > 0) {
+          unB = unW[q > 0 ? q - 1 : 0];
+          ueB = ueW[q > 0 ? q - 1 : 0];
+          utB = utW[q > 0 ? q - 1 : 0];
+        } else if (w > 0) {
+          const double *Ep = exB + (size_t)buf * 3 * NW * 32;
+          unB = Ep[(0 * NW + w - 1) * 32 + lane];
+          ueB = Ep[(1 * NW + w - 1) * 32 + lane];
+          utB = Ep[(2 * NW + w - 1) * 32 + lane];
+        } else {
+          unB = hK[0];
+          ueB = hK[1];
+          utB = hK[2];
         }
-        if (g.dk == B.TK - 1 && g.hasT) {
-          uint64_t *f = faceK(myf, B, t, g.dj, W);
-          Face<double>::put(f, UN, ep);
-          Face<double>::put(f + 2, UE, ep);
-          Face<double>::put(f + 4, UT, ep);
+        const double LB = ab / (1.0 + al * (unB + ueB));
+        const double LW = aw / (1.0 + al * (unW[q] + utW[q]));
+        const double LS = as / (1.0 + al * (ueS + utS));
+        const double P1 = al * (LB * unB + LW * unW[q]);
+        const double P2 = al * (LB * ueB + LS * ueS);
+        const double P3 = al * (LW * utW[q] + LS * utS);
+        const double LP = ap + P1 + P2 + P3 - LB * utB - LW * ueW[q] - LS * unS;
+        double UN = 0, UE = 0, UT = 0;
+        if (act) {
+          UN = (an - P1) / LP;
+          UE = (ae - P2) / LP;
+          UT = (at - P3) / LP;
+          const double RLP = 1.0 / LP;
+          if (LP == 0.0 || !isfinite(RLP) || !isfinite(LB) || !isfinite(LW) || !isfinite(LS) ||
+              !isfinite(UN) || !isfinite(UE) || !isfinite(UT) || !isfinite(LP))
+            atomicCAS(c.status, DEV_OK, DEV_BREAKDOWN);
+          const long long cell = B.cell0 + rb(g.s0 + t, g.k(q)) + g.j;
+          TF *fr = P.recF + cell * P.rsf;
+          fr[REC_LB] = (TF)LB;
+          fr[REC_LW] = (TF)LW;
+          fr[REC_LS] = (TF)LS;
+          fr[REC_RLP] = (TF)RLP;
+          TF *br = P.recB + cell * 4;
+          br[RECB_UE] = (TF)UE;
+          br[RECB_UN] = (TF)UN;
+          br[RECB_UT] = (TF)UT;
+          br[3] = (TF)0;
+          if (lane == kTJ - 1 && g.hasN) {
+            uint64_t *f = faceJ(myf, B, t, g.dk(q), W);
+            Face<double>::put(f, UN, ep);
+            Face<double>::put(f + 2, UE, ep);
+            Face<double>::put(f + 4, UT, ep);
+          }
+          if (q == Q - 1 && g.eT && g.hasT) {
+            uint64_t *f = faceK(myf, B, t, lane, W);
+            Face<double>::put(f, UN, ep);
+            Face<double>::put(f + 2, UE, ep);
+            Face<double>::put(f + 4, UT, ep);
+          }
         }
+        nUN[q] = UN;
+        nUE[q] = UE;
+        nUT[q] = UT;
       }
-      unW = UN;
-      ueW = UE;
-      utW = UT;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        unW[q] = nUN[q];
+        ueW[q] = nUE[q];
+        utW[q] = nUT[q];
+      }
     }
     cp_async_wait<0>();
+    if (tr && threadIdx.x == 0) tr[2] = gtimer();
     __syncthreads();
   }
 }
@@ -391,49 +494,36 @@ __global__ void __launch_bounds__(512) k_factor(FacParams P) {
 // ============================================================ forward sweep
 // resforward3d: r = b - A x (norm of r), then y = L^{-1} r with
 //   y_P = (r_P - LB y_B - LW y_W - LS y_S) * (1/LP).
-// SYM: A symmetric, only AP, AE, AN, AT are read; AW(P) = AE(W),
+// SYM: A symmetric, only AP, AE, AN, AT are stored; AW(P) = AE(W),
 //      AS(P) = AN(S), AB(P) = AT(B) (the paper's Listing 1).
 // ZX:  x = 0, so r = b (first inner iteration of the refinement).
-// Staged values per thread and step (slot index):
-template <bool SYM, bool ZX>
-struct FwdSlots {
-  // general: ap aw ae as an ab at lb lw ls rlp b xp1 hxj hxk
-  // sym:     ap ae an at lb lw ls rlp b xp1 hxj hxk hanS hatB
-  // zx:      lb lw ls rlp b
-  static constexpr int NA = ZX ? 0 : (SYM ? 4 : 7);
-  static constexpr int LB = NA, LW = NA + 1, LS = NA + 2, RLP = NA + 3, B = NA + 4;
-  static constexpr int XP1 = NA + 5, HXJ = NA + 6, HXK = NA + 7;
-  static constexpr int HANS = NA + 8, HATB = NA + 9;
-  static constexpr int NV = ZX ? 5 : (SYM ? 14 : 15);
-  static constexpr int NE = ZX ? 1 : (SYM ? 5 : 3);  // exchanged values: [ym1] or [xm1 xp1 ym1 (anm1 atm1)]
-};
-
-template <typename T, bool SYM, bool ZX, bool NORM, int R>
+template <typename T, bool SYM, bool ZX, bool NORM, int Q, int R>
 __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
   static_assert(!(SYM && ZX), "x = 0 needs no matrix");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_claim;
+  __shared__ int s_claim, s_blk;
   __shared__ double s_red[32];
-  using S = FwdSlots<SYM, ZX>;
-  constexpr int NV = S::NV, NE = S::NE, W = 2;
+  constexpr int W = 2;
+  constexpr int RSS = ZX ? 4 : fwd_rec_values(SYM);  // staged values per record (from its start)
+  constexpr int NCP = RSS * (int)sizeof(T) / 16;
+  // scalar slots: per row b, x(i+1), halo x (j), halo AN (j, symmetric); then halo x (k below / above), halo AT
+  constexpr int SB = 0, SXP = Q, SHJ = 2 * Q, SHA = 3 * Q;
+  constexpr int SHKB = SYM ? 4 * Q : 3 * Q, SHKT = SHKB + 1, SHAB = SHKB + 2;
+  constexpr int AO_AP = SYM ? RECS_AP : RECG_AP;
   const SweepCommon &c = P.c;
   const unsigned ep = sweep_prologue(c);
+  if (threadIdx.x == 0) s_blk = -1;
   // block-uniform exit decision (the status word may change during the launch)
   if (__syncthreads_or(c.ctl->done || ld_relaxed(c.status) != DEV_OK)) return;
   const unsigned expect = ep + (c.stall ? 0x40000000u : 0u);
   const int NT = blockDim.x, tid = threadIdx.x;
-  const int EC = c.exch_cells, FS = c.face_slots;
-  Smem<T> sm(smem_raw, R, NV, NT, NE, EC);
-  const T *src[S::NA > 0 ? S::NA : 1];
-  if constexpr (!ZX) {
-    if constexpr (SYM) {
-      src[0] = P.ap; src[1] = P.ae; src[2] = P.an; src[3] = P.at;
-    } else {
-      src[0] = P.ap; src[1] = P.aw; src[2] = P.ae; src[3] = P.as;
-      src[4] = P.an; src[5] = P.ab; src[6] = P.at;
-    }
-  }
-  constexpr int EB = (int)sizeof(T);
+  const SweepLayout L = fwd_layout((int)sizeof(T), SYM, ZX, Q, R, NT, c.tab_ints);
+  int *sPO = reinterpret_cast<int *>(smem_raw);
+  unsigned char *stage = smem_raw + L.tab;
+  constexpr int NEB = ZX ? 1 : (SYM ? 3 : 2);  // published by a warp's last row: ym1, xm1, atm1
+  T *exB = reinterpret_cast<T *>(stage + (size_t)R * L.step);  // [2][NEB][NW][32]
+  uint64_t *fst = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(exB) + L.exch);
+  const int FS = L.fs;
   bool abort = false;
 
   for (;;) {
@@ -441,162 +531,198 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
     if (m >= c.ntiles) break;
     const Tile tl = c.tiles[m];
     const DevBlock B = c.blocks[tl.blk];
-    const ColGeom g(B, tl);
-    const int *rbk = B.rbT + (long long)min(g.k, B.nz - 1) * B.nplanes;
-    const int *rbkB = B.rbT + (long long)max(g.k - 1, 0) * B.nplanes;
-    const int *rbkT = B.rbT + (long long)min(g.k + 1, B.nz - 1) * B.nplanes;
+    unsigned long long *tr = c.trace ? c.trace + (size_t)tl.gtile * kTraceWords : nullptr;
+    load_tables(B, tl.blk, sPO, &s_blk);
+    const int *sF = sPO + B.nplanes;
+    const Geo<Q> g(B, tl);
+    const int NW = g.NW, lane = g.lane, w = g.w;
+    T *exT = exB + (size_t)2 * NEB * NW * 32;  // [2][NW][32]
     uint64_t *myf = tile_faces(c, B, tl.gtile);
     uint64_t *upJ = g.hasS ? tile_faces(c, B, tl.gtile - 1) : nullptr;
     uint64_t *upK = g.hasB ? tile_faces(c, B, tl.gtile - B.nTJ) : nullptr;
-    const int TJ2 = B.TJ + 2;
-    const int me = (g.dk + 1) * TJ2 + g.dj + 1;
-    const bool eS = g.dj == 0, eN = g.dj == B.TJ - 1, eB = g.dk == 0, eT = g.dk == B.TK - 1;
-    const bool cJ = eS && g.hasS, cK = eB && g.hasB;  // face consumers
     {
       const int lead = min(R + 1, B.nx - 1);
-      slack_gate<W>(upJ ? faceJ(upJ, B, lead + B.TJ - 1, 0, W) : nullptr,
-                    upK ? faceK(upK, B, lead + B.TK - 1, 0, W) : nullptr, expect, c, abort);
+      slack_gate<W>(upJ ? faceJ(upJ, B, lead + kTJ - 1, 0, W) : nullptr,
+                    upK ? faceK(upK, B, lead + g.TK - 1, 0, W) : nullptr, expect, c, abort, tr);
     }
+    auto rb = [&](int s, int k) { return plane_row_base(sPO, sF, B.mmax, B.nx, s, k); };
 
     auto issue = [&](int tt) {
       if (tt < g.nsteps) {
-        const int i = tt - g.dj - g.dk;
         const int s = g.s0 + tt;
-        const bool v = g.col && i >= 0 && i < B.nx;
-        const long long a = v ? B.cell0 + rbk[s] + g.j : 0;
-        T *st = sm.stage + (size_t)(tt % R) * NV * NT + tid;
-        if constexpr (!ZX) {
+        unsigned char *st = stage + (size_t)(tt % R) * L.step;
+        T *sc = reinterpret_cast<T *>(st + L.rec) + tid;
+        uint64_t *fs = fst + (size_t)(tt % R) * FS * W;
 #pragma unroll
-          for (int q = 0; q < S::NA; ++q) cp_async_zfill<EB>(st + q * NT, src[q] + a, v);
-        }
-        cp_async_zfill<EB>(st + S::LB * NT, P.lb + a, v);
-        cp_async_zfill<EB>(st + S::LW * NT, P.lw + a, v);
-        cp_async_zfill<EB>(st + S::LS * NT, P.ls + a, v);
-        cp_async_zfill<EB>(st + S::RLP * NT, P.rlp + a, v);
-        cp_async_zfill<EB>(st + S::B * NT, P.b + a, v);
-        if constexpr (!ZX) {
-          const bool vp = g.col && i + 1 >= 0 && i + 1 < B.nx;
-          const long long ap1 = vp ? B.cell0 + rbk[s + 1] + g.j : 0;
-          cp_async_zfill<EB>(st + S::XP1 * NT, P.x + ap1, vp);
-          // halo x across the tile's j faces (S for dj = 0, N for dj = TJ-1)
-          long long hj = 0;
-          bool vj = false;
-          if (eS && g.hasS && v) { hj = B.cell0 + rbk[s - 1] + g.j0 - 1; vj = true; }
-          else if (eN && g.hasN && v) { hj = B.cell0 + rbk[s + 1] + g.j0 + B.TJ; vj = true; }
-          cp_async_zfill<EB>(st + S::HXJ * NT, P.x + hj, vj);
-          long long hk = 0;
-          bool vk = false;
-          if (eB && g.hasB && v) { hk = B.cell0 + rbkB[s - 1] + g.j; vk = true; }
-          else if (eT && g.hasT && v) { hk = B.cell0 + rbkT[s + 1] + g.j; vk = true; }
-          cp_async_zfill<EB>(st + S::HXK * NT, P.x + hk, vk);
-          if constexpr (SYM) {
-            cp_async_zfill<EB>(st + S::HANS * NT, P.an + hj, vj && eS);
-            cp_async_zfill<EB>(st + S::HATB * NT, P.at + hk, vk && eB);
+        for (int q = 0; q < Q; ++q) {
+          const int i = g.i(tt, q);
+          const bool colq = g.col(B, q);
+          const bool v = colq && i >= 0 && i < B.nx;
+          const long long a = v ? B.cell0 + rb(s, g.k(q)) + g.j : 0;
+          unsigned char *d = st + ((size_t)q * NT + tid) * (RSS * sizeof(T));
+          const unsigned char *src = reinterpret_cast<const unsigned char *>(P.rec + a * P.rsf);
+#pragma unroll
+          for (int z = 0; z < NCP; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v);
+          cp_async_zfill<sizeof(T)>(sc + (SB + q) * NT, P.b + a, v);
+          if constexpr (!ZX) {
+            const bool vp = colq && i + 1 >= 0 && i + 1 < B.nx;
+            const long long ap1 = vp ? B.cell0 + rb(s + 1, g.k(q)) + g.j : 0;
+            cp_async_zfill<sizeof(T)>(sc + (SXP + q) * NT, P.x + ap1, vp);
+            long long hj = 0;
+            bool vj = false;
+            if (lane == 0 && g.hasS && v) {
+              hj = B.cell0 + rb(s - 1, g.k(q)) + g.j0 - 1;
+              vj = true;
+            } else if (lane == kTJ - 1 && g.hasN && v) {
+              hj = B.cell0 + rb(s + 1, g.k(q)) + g.j0 + kTJ;
+              vj = true;
+            }
+            cp_async_zfill<sizeof(T)>(sc + (SHJ + q) * NT, P.x + hj, vj);
+            if constexpr (SYM) cp_async_zfill<sizeof(T)>(sc + (SHA + q) * NT, P.rec + hj * P.rsf + RECS_AN, vj && lane == 0);
+            if (q == 0 && g.eB) {
+              const bool vb = g.hasB && v;
+              const long long hk = vb ? B.cell0 + rb(s - 1, g.k0 - 1) + g.j : 0;
+              cp_async_zfill<sizeof(T)>(sc + SHKB * NT, P.x + hk, vb);
+              if constexpr (SYM) cp_async_zfill<sizeof(T)>(sc + SHAB * NT, P.rec + hk * P.rsf + RECS_AT, vb);
+            }
+            if (q == Q - 1 && g.eT) {
+              const bool vt = g.hasT && v;
+              const long long hk = vt ? B.cell0 + rb(s + 1, g.k0 + g.TK) + g.j : 0;
+              cp_async_zfill<sizeof(T)>(sc + SHKT * NT, P.x + hk, vt);
+            }
           }
+          if (lane == 0 && g.hasS && v) rec_prefetch<W>(fs + g.dk(q) * W, faceJ(upJ, B, tt + kTJ - 1, g.dk(q), W));
+          if (q == 0 && g.eB && g.hasB && v)
+            rec_prefetch<W>(fs + (g.TK + lane) * W, faceK(upK, B, tt + g.TK - 1, lane, W));
         }
-        uint64_t *fs = sm.fst + (size_t)(tt % R) * FS * W;
-        if (cJ && v) rec_prefetch<W>(fs + g.dk * W, faceJ(upJ, B, tt + B.TJ - 1, g.dk, W));
-        if (cK && v) rec_prefetch<W>(fs + (B.TK + g.dj) * W, faceK(upK, B, tt + B.TK - 1, g.dj, W));
       }
       cp_async_commit();
     };
 #pragma unroll
     for (int tt = 0; tt < R - 1; ++tt) issue(tt);
 
-    T xm1 = 0, x0 = 0, ym1 = 0, aem1 = 0, anm1 = 0, atm1 = 0;
+    T xm1[Q], x0[Q], ym1[Q], aem1[Q], anm1[Q], atm1[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) xm1[q] = x0[q] = ym1[q] = aem1[q] = anm1[q] = atm1[q] = T(0);
     double acc = 0.0;
     // x of a column's first cell normally arrives as the previous step's x(i+1);
     // the tile's corner column starts at i = 0 on step 0, so it reads it here
     if constexpr (!ZX) {
-      if (g.dj == 0 && g.dk == 0 && g.col) x0 = P.x[B.cell0 + rbk[g.s0] + g.j];
+      if (lane == 0 && w == 0 && g.col(B, 0)) x0[0] = P.x[B.cell0 + rb(g.s0, g.k0) + g.j];
     }
     for (int t = 0; t < g.nsteps; ++t) {
       issue(t + R - 1);
       cp_async_wait<R - 1>();
-      const T *st = sm.stage + (size_t)(t % R) * NV * NT + tid;
-      const uint64_t *fs = sm.fst + (size_t)(t % R) * FS * W;
-      const int i = t - g.dj - g.dk;
-      const bool act = g.col && i >= 0 && i < B.nx;
-      T *E = sm.exch + (size_t)(t & 1) * NE * EC;
-      T *EY = E + (ZX ? 0 : 2) * EC;  // ym1 plane
-      T xp1 = 0;
+      const unsigned char *st = stage + (size_t)(t % R) * L.step;
+      const T *sc = reinterpret_cast<const T *>(st + L.rec) + tid;
+      const uint64_t *fs = fst + (size_t)(t % R) * FS * W;
+      const int buf = t & 1;
+      T xp1[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) xp1[q] = ZX ? T(0) : sc[(SXP + q) * NT];
+      T *E = exB + (size_t)buf * NEB * NW * 32;
+      E[(0 * NW + w) * 32 + lane] = ym1[Q - 1];
       if constexpr (!ZX) {
-        xp1 = st[S::XP1 * NT];
-        E[me] = xm1;
-        E[EC + me] = xp1;
-        if constexpr (SYM) {
-          E[3 * EC + me] = anm1;
-          E[4 * EC + me] = atm1;
-        }
+        E[(1 * NW + w) * 32 + lane] = xm1[Q - 1];
+        if constexpr (SYM) E[(2 * NW + w) * 32 + lane] = atm1[Q - 1];
+        exT[((size_t)buf * NW + w) * 32 + lane] = xp1[0];
       }
-      EY[me] = ym1;
-      if (eS) {
-        uint64_t w[W] = {0, 0};
-        if (act && cJ) rec_take<W>(fs + g.dk * W, faceJ(upJ, B, t + B.TJ - 1, g.dk, W), expect, w, c, abort);
-        EY[me - 1] = Face<T>::get(w);
-        if constexpr (!ZX) {
-          E[me - 1] = st[S::HXJ * NT];
-          if constexpr (SYM) E[3 * EC + me - 1] = st[S::HANS * NT];
-        }
-      }
-      if constexpr (!ZX) {
-        if (eN) E[EC + me + 1] = st[S::HXJ * NT];
-        if (eT) E[EC + me + TJ2] = st[S::HXK * NT];
-      }
-      if (eB) {
-        uint64_t w[W] = {0, 0};
-        if (act && cK)
-          rec_take<W>(fs + (B.TK + g.dj) * W, faceK(upK, B, t + B.TK - 1, g.dj, W), expect, w, c, abort);
-        EY[me - TJ2] = Face<T>::get(w);
-        if constexpr (!ZX) {
-          E[me - TJ2] = st[S::HXK * NT];
-          if constexpr (SYM) E[4 * EC + me - TJ2] = st[S::HATB * NT];
+      T yK = T(0);
+      if (g.eB) {
+        const int i0 = g.i(t, 0);
+        if (g.hasB && g.col(B, 0) && i0 >= 0 && i0 < B.nx) {
+          uint64_t wv[W];
+          rec_take<W>(fs + (g.TK + lane) * W, faceK(upK, B, t + g.TK - 1, lane, W), expect, wv, c, abort, tr);
+          yK = Face<T>::get(wv);
         }
       }
       __syncthreads();
-      T r = st[S::B * NT];
-      if constexpr (!ZX) {
-        const T xS = E[me - 1], xN = E[EC + me + 1], xB = E[me - TJ2], xT = E[EC + me + TJ2];
-        if constexpr (SYM) {
-          const T ap = st[0], ae = st[NT], an = st[2 * NT], at = st[3 * NT];
-          const T asv = E[3 * EC + me - 1], abv = E[4 * EC + me - TJ2];
-          r = fma(-ap, x0, r);
-          r = fma(-aem1, xm1, r);
-          r = fma(-ae, xp1, r);
-          r = fma(-asv, xS, r);
-          r = fma(-an, xN, r);
-          r = fma(-abv, xB, r);
-          r = fma(-at, xT, r);
-          aem1 = ae;
-          anm1 = an;
-          atm1 = at;
-        } else {
-          r = fma(-st[0], x0, r);
-          r = fma(-st[NT], xm1, r);
-          r = fma(-st[2 * NT], xp1, r);
-          r = fma(-st[3 * NT], xS, r);
-          r = fma(-st[4 * NT], xN, r);
-          r = fma(-st[5 * NT], xB, r);
-          r = fma(-st[6 * NT], xT, r);
+      T ny[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int i = g.i(t, q);
+        const bool act = g.col(B, q) && i >= 0 && i < B.nx;
+        const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * (RSS * sizeof(T)));
+        T r = sc[(SB + q) * NT];
+        T yS = shfl_up1(ym1[q]);
+        if (lane == 0) {
+          yS = T(0);
+          if (g.hasS && act) {
+            uint64_t wv[W];
+            rec_take<W>(fs + g.dk(q) * W, faceJ(upJ, B, t + kTJ - 1, g.dk(q), W), expect, wv, c, abort, tr);
+            yS = Face<T>::get(wv);
+          }
         }
+        T yB;
+        if (q > 0) yB = ym1[q > 0 ? q - 1 : 0];
+        else if (w > 0) yB = E[(0 * NW + w - 1) * 32 + lane];
+        else yB = yK;
+        if constexpr (!ZX) {
+          T xS = shfl_up1(xm1[q]);
+          T xN = shfl_dn1(xp1[q]);
+          if (lane == 0) xS = sc[(SHJ + q) * NT];
+          if (lane == kTJ - 1) xN = sc[(SHJ + q) * NT];
+          T xB, xT;
+          if (q > 0) xB = xm1[q > 0 ? q - 1 : 0];
+          else if (w > 0) xB = E[(1 * NW + w - 1) * 32 + lane];
+          else xB = sc[SHKB * NT];
+          if (q < Q - 1) xT = xp1[q < Q - 1 ? q + 1 : 0];
+          else if (w < NW - 1) xT = exT[((size_t)buf * NW + w + 1) * 32 + lane];
+          else xT = sc[SHKT * NT];
+          if constexpr (SYM) {
+            const T ap = rec[RECS_AP], ae = rec[RECS_AE], an = rec[RECS_AN], at = rec[RECS_AT];
+            T asv = shfl_up1(anm1[q]);
+            if (lane == 0) asv = sc[(SHA + q) * NT];
+            T abv;
+            if (q > 0) abv = atm1[q > 0 ? q - 1 : 0];
+            else if (w > 0) abv = E[(2 * NW + w - 1) * 32 + lane];
+            else abv = sc[SHAB * NT];
+            r = fma(-ap, x0[q], r);
+            r = fma(-aem1[q], xm1[q], r);
+            r = fma(-ae, xp1[q], r);
+            r = fma(-asv, xS, r);
+            r = fma(-an, xN, r);
+            r = fma(-abv, xB, r);
+            r = fma(-at, xT, r);
+          } else {
+            r = fma(-rec[RECG_AP], x0[q], r);
+            r = fma(-rec[RECG_AW], xm1[q], r);
+            r = fma(-rec[RECG_AE], xp1[q], r);
+            r = fma(-rec[RECG_AS], xS, r);
+            r = fma(-rec[RECG_AN], xN, r);
+            r = fma(-rec[RECG_AB], xB, r);
+            r = fma(-rec[RECG_AT], xT, r);
+          }
+        }
+        T y = fma(-rec[REC_LB], yB, r);
+        y = fma(-rec[REC_LW], ym1[q], y);
+        y = fma(-rec[REC_LS], yS, y);
+        y = y * rec[REC_RLP];
+        if constexpr (NORM) acc = fma((double)r, (double)r, acc);
+        if (act) {
+          const long long a = B.cell0 + rb(g.s0 + t, g.k(q)) + g.j;
+          P.y[a] = y;
+          if (lane == kTJ - 1 && g.hasN) Face<T>::put(faceJ(myf, B, t, g.dk(q), W), y, ep);
+          if (q == Q - 1 && g.eT && g.hasT) Face<T>::put(faceK(myf, B, t, lane, W), y, ep);
+        }
+        ny[q] = act ? y : T(0);
       }
-      const T yS = EY[me - 1], yB = EY[me - TJ2];
-      T y = fma(-st[S::LB * NT], yB, r);
-      y = fma(-st[S::LW * NT], ym1, y);
-      y = fma(-st[S::LS * NT], yS, y);
-      y = y * st[S::RLP * NT];
-      if constexpr (NORM) acc = fma((double)r, (double)r, acc);
-      if (act) {
-        const long long a = B.cell0 + rbk[g.s0 + t] + g.j;
-        P.y[a] = y;
-        if (eN && g.hasN) Face<T>::put(faceJ(myf, B, t, g.dk, W), y, ep);
-        if (eT && g.hasT) Face<T>::put(faceK(myf, B, t, g.dj, W), y, ep);
+      // rotate the column state (the last loop read the pre-rotation values)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        if constexpr (SYM) {
+          const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * (RSS * sizeof(T)));
+          aem1[q] = rec[RECS_AE];
+          anm1[q] = rec[RECS_AN];
+          atm1[q] = rec[RECS_AT];
+        }
+        xm1[q] = x0[q];
+        x0[q] = xp1[q];
+        ym1[q] = ny[q];
       }
-      xm1 = x0;
-      x0 = xp1;
-      ym1 = act ? y : T(0);
     }
     cp_async_wait<0>();
+    if (tr && threadIdx.x == 0) tr[2] = gtimer();
     if constexpr (NORM) {
       const double tot = block_sum(acc, s_red);
       if (tid == 0) P.partials[tl.gtile] = tot;
@@ -610,21 +736,25 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
 // (descending planes), x_P <- x_P + d_P.  ZX: x = 0 on entry (x_P <- d_P).
 // UPD64 (refined mode, last inner iteration): x64_P += (double) x_P instead
 // of storing x_P.
-template <typename T, bool ZX, bool UPD64, int R>
+template <typename T, bool ZX, bool UPD64, int Q, int R>
 __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_claim;
-  constexpr int NV = (ZX ? 4 : 5) + (UPD64 ? 2 : 0);  // ue un ut y [x] [x64 as 2 slots]
+  __shared__ int s_claim, s_blk;
   constexpr int W = 2;
+  constexpr int SY = 0, SX = Q;  // scalar slots
   const SweepCommon &c = P.c;
   const unsigned ep = sweep_prologue(c);
+  if (threadIdx.x == 0) s_blk = -1;
   // block-uniform exit decision (the status word may change during the launch)
   if (__syncthreads_or(c.ctl->done || ld_relaxed(c.status) != DEV_OK)) return;
   const unsigned expect = ep + (c.stall ? 0x40000000u : 0u);
   const int NT = blockDim.x, tid = threadIdx.x;
-  const int EC = c.exch_cells, FS = c.face_slots;
-  Smem<T> sm(smem_raw, R, NV, NT, 1, EC);
-  constexpr int EB = (int)sizeof(T);
+  const SweepLayout L = bwd_layout((int)sizeof(T), ZX, UPD64, Q, R, NT, c.tab_ints);
+  int *sPO = reinterpret_cast<int *>(smem_raw);
+  unsigned char *stage = smem_raw + L.tab;
+  T *exT = reinterpret_cast<T *>(stage + (size_t)R * L.step);  // [2][NW][32]: row 0 of each warp
+  uint64_t *fst = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(exT) + L.exch);
+  const int FS = L.fs;
   bool abort = false;
 
   for (;;) {
@@ -632,94 +762,121 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
     if (m >= c.ntiles) break;
     const Tile tl = c.tiles[m];
     const DevBlock B = c.blocks[tl.blk];
-    const ColGeom g(B, tl);
-    const int *rbk = B.rbT + (long long)min(g.k, B.nz - 1) * B.nplanes;
+    unsigned long long *tr = c.trace ? c.trace + (size_t)tl.gtile * kTraceWords : nullptr;
+    load_tables(B, tl.blk, sPO, &s_blk);
+    const int *sF = sPO + B.nplanes;
+    const Geo<Q> g(B, tl);
+    const int NW = g.NW, lane = g.lane, w = g.w;
     uint64_t *myf = tile_faces(c, B, tl.gtile);
     uint64_t *dnJ = g.hasN ? tile_faces(c, B, tl.gtile + 1) : nullptr;
     uint64_t *dnK = g.hasT ? tile_faces(c, B, tl.gtile + B.nTJ) : nullptr;
-    const int TJ2 = B.TJ + 2;
-    const int me = (g.dk + 1) * TJ2 + g.dj + 1;
     const int last = g.nsteps - 1;
-    const bool cJ = g.dj == B.TJ - 1 && g.hasN, cK = g.dk == B.TK - 1 && g.hasT;  // face consumers
     {
       // the consumer of the last valid row (column) needs, `lead` steps into
       // the walk, cell i = nx-1-lead, published on the producer's step i + lane
       const int lead = min(R + 1, B.nx - 1);
       const int i = B.nx - 1 - lead;
       slack_gate<W>(dnJ ? faceJ(dnJ, B, i + g.nkt - 1, g.nkt - 1, W) : nullptr,
-                    dnK ? faceK(dnK, B, i + g.njt - 1, g.njt - 1, W) : nullptr, expect, c, abort);
+                    dnK ? faceK(dnK, B, i + g.njt - 1, g.njt - 1, W) : nullptr, expect, c, abort, tr);
     }
+    auto rb = [&](int s, int k) { return plane_row_base(sPO, sF, B.mmax, B.nx, s, k); };
 
     // backward step u processes local plane t = last - u
     auto issue = [&](int uu) {
       if (uu < g.nsteps) {
         const int t = last - uu;
-        const int i = t - g.dj - g.dk;
-        const bool v = g.col && i >= 0 && i < B.nx;
-        const long long a = v ? B.cell0 + rbk[g.s0 + t] + g.j : 0;
-        T *st = sm.stage + (size_t)(uu % R) * NV * NT + tid;
-        cp_async_zfill<EB>(st, P.ue + a, v);
-        cp_async_zfill<EB>(st + NT, P.un + a, v);
-        cp_async_zfill<EB>(st + 2 * NT, P.ut + a, v);
-        cp_async_zfill<EB>(st + 3 * NT, P.y + a, v);
-        if constexpr (!ZX) cp_async_zfill<EB>(st + 4 * NT, P.x + a, v);
-        if constexpr (UPD64) {
-          double *s64 = reinterpret_cast<double *>(sm.stage + (size_t)(uu % R) * NV * NT + (NV - 2) * NT) + tid;
-          cp_async_zfill<8>(s64, P.x64 + a, v);
+        const int s = g.s0 + t;
+        unsigned char *st = stage + (size_t)(uu % R) * L.step;
+        double *s64 = reinterpret_cast<double *>(st + L.rec) + tid;
+        T *sc = reinterpret_cast<T *>(st + L.rec + L.aux) + tid;
+        uint64_t *fs = fst + (size_t)(uu % R) * FS * W;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const int i = g.i(t, q);
+          const bool v = g.col(B, q) && i >= 0 && i < B.nx;
+          const long long a = v ? B.cell0 + rb(s, g.k(q)) + g.j : 0;
+          unsigned char *d = st + ((size_t)q * NT + tid) * (4 * sizeof(T));
+          const unsigned char *src = reinterpret_cast<const unsigned char *>(P.rec + a * 4);
+#pragma unroll
+          for (int z = 0; z < (int)sizeof(T) / 4; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v);
+          cp_async_zfill<sizeof(T)>(sc + (SY + q) * NT, P.y + a, v);
+          if constexpr (!ZX) cp_async_zfill<sizeof(T)>(sc + (SX + q) * NT, P.x + a, v);
+          if constexpr (UPD64) cp_async_zfill<8>(s64 + (size_t)q * NT, P.x64 + a, v);
+          if (lane == kTJ - 1 && g.hasN && v)
+            rec_prefetch<W>(fs + g.dk(q) * W, faceJ(dnJ, B, t - (kTJ - 1), g.dk(q), W));
+          if (q == Q - 1 && g.eT && g.hasT && v)
+            rec_prefetch<W>(fs + (g.TK + lane) * W, faceK(dnK, B, t - (g.TK - 1), lane, W));
         }
-        uint64_t *fs = sm.fst + (size_t)(uu % R) * FS * W;
-        if (cJ && v) rec_prefetch<W>(fs + g.dk * W, faceJ(dnJ, B, t - (B.TJ - 1), g.dk, W));
-        if (cK && v) rec_prefetch<W>(fs + (B.TK + g.dj) * W, faceK(dnK, B, t - (B.TK - 1), g.dj, W));
       }
       cp_async_commit();
     };
 #pragma unroll
     for (int uu = 0; uu < R - 1; ++uu) issue(uu);
 
-    T dE = 0;
+    T dE[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) dE[q] = T(0);
     for (int u = 0; u < g.nsteps; ++u) {
       issue(u + R - 1);
       cp_async_wait<R - 1>();
-      const T *st = sm.stage + (size_t)(u % R) * NV * NT + tid;
-      const uint64_t *fs = sm.fst + (size_t)(u % R) * FS * W;
+      const unsigned char *st = stage + (size_t)(u % R) * L.step;
+      const double *s64 = reinterpret_cast<const double *>(st + L.rec) + tid;
+      const T *sc = reinterpret_cast<const T *>(st + L.rec + L.aux) + tid;
+      const uint64_t *fs = fst + (size_t)(u % R) * FS * W;
       const int t = last - u;
-      const int i = t - g.dj - g.dk;
-      const bool act = g.col && i >= 0 && i < B.nx;
-      T *E = sm.exch + (size_t)(u & 1) * EC;
-      E[me] = dE;
-      if (g.dj == B.TJ - 1) {
-        uint64_t w[W] = {0, 0};
-        if (act && cJ) rec_take<W>(fs + g.dk * W, faceJ(dnJ, B, t - (B.TJ - 1), g.dk, W), expect, w, c, abort);
-        E[me + 1] = Face<T>::get(w);
-      }
-      if (g.dk == B.TK - 1) {
-        uint64_t w[W] = {0, 0};
-        if (act && cK)
-          rec_take<W>(fs + (B.TK + g.dj) * W, faceK(dnK, B, t - (B.TK - 1), g.dj, W), expect, w, c, abort);
-        E[me + TJ2] = Face<T>::get(w);
+      const int buf = u & 1;
+      exT[((size_t)buf * NW + w) * 32 + lane] = dE[0];
+      T dK = T(0);
+      if (g.eT) {
+        const int iq = g.i(t, Q - 1);
+        if (g.hasT && g.col(B, Q - 1) && iq >= 0 && iq < B.nx) {
+          uint64_t wv[W];
+          rec_take<W>(fs + (g.TK + lane) * W, faceK(dnK, B, t - (g.TK - 1), lane, W), expect, wv, c, abort, tr);
+          dK = Face<T>::get(wv);
+        }
       }
       __syncthreads();
-      const T dN = E[me + 1], dT = E[me + TJ2];
-      T d = fma(-st[0], dE, st[3 * NT]);
-      d = fma(-st[NT], dN, d);
-      d = fma(-st[2 * NT], dT, d);
-      if (act) {
-        const long long a = B.cell0 + rbk[g.s0 + t] + g.j;
-        T xn = d;
-        if constexpr (!ZX) xn = st[4 * NT] + d;
-        if constexpr (UPD64) {
-          const double *s64 =
-              reinterpret_cast<const double *>(sm.stage + (size_t)(u % R) * NV * NT + (NV - 2) * NT) + tid;
-          P.x64[a] = *s64 + (double)xn;
-        } else {
-          P.x[a] = xn;
+      T nd[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int i = g.i(t, q);
+        const bool act = g.col(B, q) && i >= 0 && i < B.nx;
+        const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * (4 * sizeof(T)));
+        T dN = shfl_dn1(dE[q]);
+        if (lane == kTJ - 1) {
+          dN = T(0);
+          if (g.hasN && act) {
+            uint64_t wv[W];
+            rec_take<W>(fs + g.dk(q) * W, faceJ(dnJ, B, t - (kTJ - 1), g.dk(q), W), expect, wv, c, abort, tr);
+            dN = Face<T>::get(wv);
+          }
         }
-        if (g.dj == 0 && g.hasS) Face<T>::put(faceJ(myf, B, t, g.dk, W), d, ep);
-        if (g.dk == 0 && g.hasB) Face<T>::put(faceK(myf, B, t, g.dj, W), d, ep);
+        T dT;
+        if (q < Q - 1) dT = dE[q < Q - 1 ? q + 1 : 0];
+        else if (w < NW - 1) dT = exT[((size_t)buf * NW + w + 1) * 32 + lane];
+        else dT = dK;
+        T d = fma(-rec[RECB_UE], dE[q], sc[(SY + q) * NT]);
+        d = fma(-rec[RECB_UN], dN, d);
+        d = fma(-rec[RECB_UT], dT, d);
+        if (act) {
+          const long long a = B.cell0 + rb(g.s0 + t, g.k(q)) + g.j;
+          T xn = d;
+          if constexpr (!ZX) xn = sc[(SX + q) * NT] + d;
+          if constexpr (UPD64) {
+            P.x64[a] = s64[(size_t)q * NT] + (double)xn;
+          } else {
+            P.x[a] = xn;
+          }
+          if (lane == 0 && g.hasS) Face<T>::put(faceJ(myf, B, t, g.dk(q), W), d, ep);
+          if (q == 0 && g.eB && g.hasB) Face<T>::put(faceK(myf, B, t, lane, W), d, ep);
+        }
+        nd[q] = act ? d : T(0);
       }
-      dE = act ? d : T(0);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) dE[q] = nd[q];
     }
     cp_async_wait<0>();
+    if (tr && threadIdx.x == 0) tr[2] = gtimer();
     __syncthreads();
   }
 }
@@ -727,68 +884,81 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
 // ======================================================= FP64 residual (refinement)
 // r = b - A x in FP64 arithmetic (A stored as TA, widened), sum r^2 per tile,
 // r32 = (float) r.  No recurrence: every tile is independent.
-template <typename TA, bool SYM, int R>
+template <typename TA, bool SYM, int Q, int R>
 __global__ void __launch_bounds__(512) k_resid(ResParams<TA> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_blk;
   __shared__ double s_red[32];
-  constexpr int NA = SYM ? 4 : 7;
-  constexpr int ND = 4;           // b xp1 hxj hxk
-  constexpr int NS = SYM ? 2 : 0; // hanS hatB (TA)
+  constexpr int NA = SYM ? 4 : 8;  // staged A values per row
+  constexpr int NCP = NA * (int)sizeof(TA) / 16;
+  // FP64 scalar slots: per row b, x(i+1), halo x (j); then halo x below / above
+  constexpr int SB = 0, SXP = Q, SHJ = 2 * Q, SHKB = 3 * Q, SHKT = 3 * Q + 1;
+  // symmetric halo A (TA): per row AN of (i, j0-1, k); AT of (i, j, k0-1)
+  constexpr int AHA = 0, AHB = Q;
+  constexpr int OAE = SYM ? 1 : 2, OAN = SYM ? 2 : 4, OAT = SYM ? 3 : 6;  // in the A part
+  if (threadIdx.x == 0) s_blk = -1;
   if (__syncthreads_or(P.ctl->done || ld_relaxed(P.status) != DEV_OK)) return;
   const int NT = blockDim.x, tid = threadIdx.x;
-  double *sd = reinterpret_cast<double *>(smem_raw);           // [R][ND][NT]
-  TA *sa = reinterpret_cast<TA *>(sd + (size_t)R * ND * NT);   // [R][NA+NS][NT]
-  const size_t sa_bytes = ((size_t)R * (NA + NS) * NT * sizeof(TA) + 15) & ~(size_t)15;
-  double *exch = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(sa) + sa_bytes);
-  const int EC = P.exch_cells;
-  constexpr int NE = SYM ? 4 : 2;  // xm1 xp1 (anm1 atm1)
-  constexpr int EBA = (int)sizeof(TA);
-  const TA *src[NA];
-  if constexpr (SYM) {
-    src[0] = P.ap; src[1] = P.ae; src[2] = P.an; src[3] = P.at;
-  } else {
-    src[0] = P.ap; src[1] = P.aw; src[2] = P.ae; src[3] = P.as;
-    src[4] = P.an; src[5] = P.ab; src[6] = P.at;
-  }
+  const SweepLayout L = res_layout((int)sizeof(TA), SYM, Q, R, NT, P.tab_ints);
+  int *sPO = reinterpret_cast<int *>(smem_raw);
+  unsigned char *stage = smem_raw + L.tab;
+  constexpr int NEB = SYM ? 2 : 1;  // published by a warp's last row: xm1 (atm1)
+  double *exB = reinterpret_cast<double *>(stage + (size_t)R * L.step);  // [2][NEB][NW][32], then exT [2][NW][32]
+  const size_t recb = lay_a16(L.rec);
 
   for (int m = blockIdx.x; m < P.ntiles; m += gridDim.x) {
     const Tile tl = P.tiles[m];
     const DevBlock B = P.blocks[tl.blk];
-    const ColGeom g(B, tl);
-    const int *rbk = B.rbT + (long long)min(g.k, B.nz - 1) * B.nplanes;
-    const int *rbkB = B.rbT + (long long)max(g.k - 1, 0) * B.nplanes;
-    const int *rbkT = B.rbT + (long long)min(g.k + 1, B.nz - 1) * B.nplanes;
-    const int TJ2 = B.TJ + 2;
-    const int me = (g.dk + 1) * TJ2 + g.dj + 1;
-    const bool eS = g.dj == 0, eN = g.dj == B.TJ - 1, eB = g.dk == 0, eT = g.dk == B.TK - 1;
+    load_tables(B, tl.blk, sPO, &s_blk);
+    const int *sF = sPO + B.nplanes;
+    const Geo<Q> g(B, tl);
+    const int NW = g.NW, lane = g.lane, w = g.w;
+    double *exT = exB + (size_t)2 * NEB * NW * 32;
+    auto rb = [&](int s, int k) { return plane_row_base(sPO, sF, B.mmax, B.nx, s, k); };
 
     auto issue = [&](int tt) {
       if (tt < g.nsteps) {
-        const int i = tt - g.dj - g.dk;
         const int s = g.s0 + tt;
-        const bool v = g.col && i >= 0 && i < B.nx;
-        const long long a = v ? B.cell0 + rbk[s] + g.j : 0;
-        double *d = sd + (size_t)(tt % R) * ND * NT + tid;
-        TA *q = sa + (size_t)(tt % R) * (NA + NS) * NT + tid;
+        unsigned char *st = stage + (size_t)(tt % R) * L.step;
+        double *sc = reinterpret_cast<double *>(st + recb) + tid;
+        TA *sa = reinterpret_cast<TA *>(st + recb + L.aux) + tid;
 #pragma unroll
-        for (int z = 0; z < NA; ++z) cp_async_zfill<EBA>(q + z * NT, src[z] + a, v);
-        cp_async_zfill<8>(d, P.b + a, v);
-        const bool vp = g.col && i + 1 >= 0 && i + 1 < B.nx;
-        const long long ap1 = vp ? B.cell0 + rbk[s + 1] + g.j : 0;
-        cp_async_zfill<8>(d + NT, P.x + ap1, vp);
-        long long hj = 0;
-        bool vj = false;
-        if (eS && g.hasS && v) { hj = B.cell0 + rbk[s - 1] + g.j0 - 1; vj = true; }
-        else if (eN && g.hasN && v) { hj = B.cell0 + rbk[s + 1] + g.j0 + B.TJ; vj = true; }
-        cp_async_zfill<8>(d + 2 * NT, P.x + hj, vj);
-        long long hk = 0;
-        bool vk = false;
-        if (eB && g.hasB && v) { hk = B.cell0 + rbkB[s - 1] + g.j; vk = true; }
-        else if (eT && g.hasT && v) { hk = B.cell0 + rbkT[s + 1] + g.j; vk = true; }
-        cp_async_zfill<8>(d + 3 * NT, P.x + hk, vk);
-        if constexpr (SYM) {
-          cp_async_zfill<EBA>(q + NA * NT, P.an + hj, vj && eS);
-          cp_async_zfill<EBA>(q + (NA + 1) * NT, P.at + hk, vk && eB);
+        for (int q = 0; q < Q; ++q) {
+          const int i = g.i(tt, q);
+          const bool colq = g.col(B, q);
+          const bool v = colq && i >= 0 && i < B.nx;
+          const long long a = v ? B.cell0 + rb(s, g.k(q)) + g.j : 0;
+          unsigned char *d = st + ((size_t)q * NT + tid) * (NA * sizeof(TA));
+          const unsigned char *src = reinterpret_cast<const unsigned char *>(P.arec + a * P.astride);
+#pragma unroll
+          for (int z = 0; z < NCP; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v);
+          cp_async_zfill<8>(sc + (SB + q) * NT, P.b + a, v);
+          const bool vp = colq && i + 1 >= 0 && i + 1 < B.nx;
+          const long long ap1 = vp ? B.cell0 + rb(s + 1, g.k(q)) + g.j : 0;
+          cp_async_zfill<8>(sc + (SXP + q) * NT, P.x + ap1, vp);
+          long long hj = 0;
+          bool vj = false;
+          if (lane == 0 && g.hasS && v) {
+            hj = B.cell0 + rb(s - 1, g.k(q)) + g.j0 - 1;
+            vj = true;
+          } else if (lane == kTJ - 1 && g.hasN && v) {
+            hj = B.cell0 + rb(s + 1, g.k(q)) + g.j0 + kTJ;
+            vj = true;
+          }
+          cp_async_zfill<8>(sc + (SHJ + q) * NT, P.x + hj, vj);
+          if constexpr (SYM)
+            cp_async_zfill<sizeof(TA)>(sa + (AHA + q) * NT, P.arec + hj * P.astride + OAN, vj && lane == 0);
+          if (q == 0 && g.eB) {
+            const bool vb = g.hasB && v;
+            const long long hk = vb ? B.cell0 + rb(s - 1, g.k0 - 1) + g.j : 0;
+            cp_async_zfill<8>(sc + SHKB * NT, P.x + hk, vb);
+            if constexpr (SYM) cp_async_zfill<sizeof(TA)>(sa + AHB * NT, P.arec + hk * P.astride + OAT, vb);
+          }
+          if (q == Q - 1 && g.eT) {
+            const bool vt = g.hasT && v;
+            const long long hk = vt ? B.cell0 + rb(s + 1, g.k0 + g.TK) + g.j : 0;
+            cp_async_zfill<8>(sc + SHKT * NT, P.x + hk, vt);
+          }
         }
       }
       cp_async_commit();
@@ -796,61 +966,80 @@ __global__ void __launch_bounds__(512) k_resid(ResParams<TA> P) {
 #pragma unroll
     for (int tt = 0; tt < R - 1; ++tt) issue(tt);
 
-    double xm1 = 0, x0 = 0, aem1 = 0, anm1 = 0, atm1 = 0, acc = 0;
-    if (g.dj == 0 && g.dk == 0 && g.col) x0 = P.x[B.cell0 + rbk[g.s0] + g.j];
+    double xm1[Q], x0[Q], aem1[Q], anm1[Q], atm1[Q], acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) xm1[q] = x0[q] = aem1[q] = anm1[q] = atm1[q] = 0.0;
+    if (lane == 0 && w == 0 && g.col(B, 0)) x0[0] = P.x[B.cell0 + rb(g.s0, g.k0) + g.j];
     for (int t = 0; t < g.nsteps; ++t) {
       issue(t + R - 1);
       cp_async_wait<R - 1>();
-      const double *d = sd + (size_t)(t % R) * ND * NT + tid;
-      const TA *q = sa + (size_t)(t % R) * (NA + NS) * NT + tid;
-      const int i = t - g.dj - g.dk;
-      const bool act = g.col && i >= 0 && i < B.nx;
-      double *E = exch + (size_t)(t & 1) * NE * EC;
-      const double xp1 = d[NT];
-      E[me] = xm1;
-      E[EC + me] = xp1;
-      if constexpr (SYM) {
-        E[2 * EC + me] = anm1;
-        E[3 * EC + me] = atm1;
-      }
-      if (eS) {
-        E[me - 1] = d[2 * NT];
-        if constexpr (SYM) E[2 * EC + me - 1] = (double)q[NA * NT];
-      }
-      if (eN) E[EC + me + 1] = d[2 * NT];
-      if (eB) {
-        E[me - TJ2] = d[3 * NT];
-        if constexpr (SYM) E[3 * EC + me - TJ2] = (double)q[(NA + 1) * NT];
-      }
-      if (eT) E[EC + me + TJ2] = d[3 * NT];
+      const unsigned char *st = stage + (size_t)(t % R) * L.step;
+      const double *sc = reinterpret_cast<const double *>(st + recb) + tid;
+      const TA *sa = reinterpret_cast<const TA *>(st + recb + L.aux) + tid;
+      const int buf = t & 1;
+      double xp1[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) xp1[q] = sc[(SXP + q) * NT];
+      double *E = exB + (size_t)buf * NEB * NW * 32;
+      E[(0 * NW + w) * 32 + lane] = xm1[Q - 1];
+      if constexpr (SYM) E[(1 * NW + w) * 32 + lane] = atm1[Q - 1];
+      exT[((size_t)buf * NW + w) * 32 + lane] = xp1[0];
       __syncthreads();
-      const double xS = E[me - 1], xN = E[EC + me + 1], xB = E[me - TJ2], xT = E[EC + me + TJ2];
-      double r = d[0];
-      if constexpr (SYM) {
-        const double ap = q[0], ae = q[NT], an = q[2 * NT], at = q[3 * NT];
-        r = fma(-ap, x0, r);
-        r = fma(-aem1, xm1, r);
-        r = fma(-ae, xp1, r);
-        r = fma(-E[2 * EC + me - 1], xS, r);
-        r = fma(-an, xN, r);
-        r = fma(-E[3 * EC + me - TJ2], xB, r);
-        r = fma(-at, xT, r);
-        aem1 = ae;
-        anm1 = an;
-        atm1 = at;
-      } else {
-        r = fma(-(double)q[0], x0, r);
-        r = fma(-(double)q[NT], xm1, r);
-        r = fma(-(double)q[2 * NT], xp1, r);
-        r = fma(-(double)q[3 * NT], xS, r);
-        r = fma(-(double)q[4 * NT], xN, r);
-        r = fma(-(double)q[5 * NT], xB, r);
-        r = fma(-(double)q[6 * NT], xT, r);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int i = g.i(t, q);
+        const bool act = g.col(B, q) && i >= 0 && i < B.nx;
+        const TA *ar = reinterpret_cast<const TA *>(st + ((size_t)q * NT + tid) * (NA * sizeof(TA)));
+        double xS = shfl_up1(xm1[q]);
+        double xN = shfl_dn1(xp1[q]);
+        if (lane == 0) xS = sc[(SHJ + q) * NT];
+        if (lane == kTJ - 1) xN = sc[(SHJ + q) * NT];
+        double xB, xT;
+        if (q > 0) xB = xm1[q > 0 ? q - 1 : 0];
+        else if (w > 0) xB = E[(0 * NW + w - 1) * 32 + lane];
+        else xB = sc[SHKB * NT];
+        if (q < Q - 1) xT = xp1[q < Q - 1 ? q + 1 : 0];
+        else if (w < NW - 1) xT = exT[((size_t)buf * NW + w + 1) * 32 + lane];
+        else xT = sc[SHKT * NT];
+        double r = sc[(SB + q) * NT];
+        if constexpr (SYM) {
+          const double ap = ar[0], ae = ar[OAE], an = ar[OAN], at = ar[OAT];
+          double asv = shfl_up1(anm1[q]);
+          if (lane == 0) asv = (double)sa[(AHA + q) * NT];
+          double abv;
+          if (q > 0) abv = atm1[q > 0 ? q - 1 : 0];
+          else if (w > 0) abv = E[(1 * NW + w - 1) * 32 + lane];
+          else abv = (double)sa[AHB * NT];
+          r = fma(-ap, x0[q], r);
+          r = fma(-aem1[q], xm1[q], r);
+          r = fma(-ae, xp1[q], r);
+          r = fma(-asv, xS, r);
+          r = fma(-an, xN, r);
+          r = fma(-abv, xB, r);
+          r = fma(-at, xT, r);
+        } else {
+          r = fma(-(double)ar[0], x0[q], r);
+          r = fma(-(double)ar[1], xm1[q], r);
+          r = fma(-(double)ar[2], xp1[q], r);
+          r = fma(-(double)ar[3], xS, r);
+          r = fma(-(double)ar[4], xN, r);
+          r = fma(-(double)ar[5], xB, r);
+          r = fma(-(double)ar[6], xT, r);
+        }
+        acc = fma(r, r, acc);
+        if (act) P.r32[B.cell0 + rb(g.s0 + t, g.k(q)) + g.j] = (float)r;
       }
-      acc = fma(r, r, acc);
-      if (act) P.r32[B.cell0 + rbk[g.s0 + t] + g.j] = (float)r;
-      xm1 = x0;
-      x0 = xp1;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        if constexpr (SYM) {
+          const TA *ar = reinterpret_cast<const TA *>(st + ((size_t)q * NT + tid) * (NA * sizeof(TA)));
+          aem1[q] = ar[OAE];
+          anm1[q] = ar[OAN];
+          atm1[q] = ar[OAT];
+        }
+        xm1[q] = x0[q];
+        x0[q] = xp1[q];
+      }
     }
     cp_async_wait<0>();
     const double tot = block_sum(acc, s_red);

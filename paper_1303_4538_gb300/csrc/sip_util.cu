@@ -5,59 +5,66 @@
 
 #include "sip_internal.h"
 #include "sip_kernels.h"
+#include "sip_layout.h"
 
 namespace sipk {
 
 // ------------------------------------------------------------ registry
-const void *kernel_ptr(int kind, int stages) {
-  const void *p = kernel_ptr_64(kind, stages);
-  return p ? p : kernel_ptr_32(kind, stages);
+const void *kernel_ptr(int kind, int Q, int R) {
+  const void *p = kernel_ptr_64(kind, Q, R);
+  if (!p) p = kernel_ptr_32(kind, Q, R);
+  if (!p) p = kernel_ptr_res(kind, Q, R);
+  return p;
 }
 
 bool kernel_is_ticketed(int kind) {
   return !(kind == K_RES64 || kind == K_RES64S || kind == K_RES32A || kind == K_RES32AS);
 }
 
-static size_t a16(size_t b) { return (b + 15) & ~(size_t)15; }
-
-// stage ring + exchange buffer (+ face ring), laid out as in sip_sweeps.cuh
-static size_t sweep_bytes(size_t r, size_t nv, size_t nt, size_t ne, size_t ec, size_t eb, size_t fs, size_t w) {
-  return a16(r * nv * nt * eb + 2 * ne * ec * eb) + r * fs * w * 8;
-}
-
-size_t kernel_smem(int kind, int R, int NT, int EC, int FS) {
-  const size_t nt = (size_t)NT, ec = (size_t)EC, r = (size_t)R, fs = (size_t)FS;
+size_t kernel_smem(int kind, int Q, int R, int NT, int tab) {
   switch (kind) {
-    case K_FACTOR: return sweep_bytes(r, 7, nt, 3, ec, 8, fs, 6);
-    case K_FWD64: return sweep_bytes(r, 15, nt, 3, ec, 8, fs, 2);
-    case K_FWD64S: return sweep_bytes(r, 14, nt, 5, ec, 8, fs, 2);
-    case K_BWD64: return sweep_bytes(r, 5, nt, 1, ec, 8, fs, 2);
+    case K_FACTOR:
+    case K_FACTOR32: return fac_layout(Q, R, NT, tab).total;
+    case K_FWD64: return fwd_layout(8, false, false, Q, R, NT, tab).total;
+    case K_FWD64S: return fwd_layout(8, true, false, Q, R, NT, tab).total;
+    case K_BWD64: return bwd_layout(8, false, false, Q, R, NT, tab).total;
     case K_FWD32:
-    case K_FWD32N: return sweep_bytes(r, 15, nt, 3, ec, 4, fs, 2);
+    case K_FWD32N: return fwd_layout(4, false, false, Q, R, NT, tab).total;
     case K_FWD32S:
-    case K_FWD32SN: return sweep_bytes(r, 14, nt, 5, ec, 4, fs, 2);
-    case K_FWD32Z: return sweep_bytes(r, 5, nt, 1, ec, 4, fs, 2);
-    case K_BWD32: return sweep_bytes(r, 5, nt, 1, ec, 4, fs, 2);
-    case K_BWD32Z: return sweep_bytes(r, 4, nt, 1, ec, 4, fs, 2);
-    case K_BWD32U: return sweep_bytes(r, 7, nt, 1, ec, 4, fs, 2);
-    case K_BWD32ZU: return sweep_bytes(r, 6, nt, 1, ec, 4, fs, 2);
-    case K_RES64: return r * 4 * nt * 8 + a16(r * 7 * nt * 8) + 2 * 2 * ec * 8;
-    case K_RES64S: return r * 4 * nt * 8 + a16(r * 6 * nt * 8) + 2 * 4 * ec * 8;
-    case K_RES32A: return r * 4 * nt * 8 + a16(r * 7 * nt * 4) + 2 * 2 * ec * 8;
-    case K_RES32AS: return r * 4 * nt * 8 + a16(r * 6 * nt * 4) + 2 * 4 * ec * 8;
+    case K_FWD32SN: return fwd_layout(4, true, false, Q, R, NT, tab).total;
+    case K_FWD32Z: return fwd_layout(4, false, true, Q, R, NT, tab).total;
+    case K_BWD32: return bwd_layout(4, false, false, Q, R, NT, tab).total;
+    case K_BWD32Z: return bwd_layout(4, true, false, Q, R, NT, tab).total;
+    case K_BWD32U: return bwd_layout(4, false, true, Q, R, NT, tab).total;
+    case K_BWD32ZU: return bwd_layout(4, true, true, Q, R, NT, tab).total;
+    case K_RES64: return res_layout(8, false, Q, R, NT, tab).total;
+    case K_RES64S: return res_layout(8, true, Q, R, NT, tab).total;
+    case K_RES32A: return res_layout(4, false, Q, R, NT, tab).total;
+    case K_RES32AS: return res_layout(4, true, Q, R, NT, tab).total;
     default: return 0;
   }
 }
 
 // ------------------------------------------------------------ layout
-// natural index p = i + nx*(j + ny*k)  ->  plan cell cell0 + rbT[k][i+j+k] + j.
+static int util_grid(long long n) {
+  long long g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+__device__ __forceinline__ long long plan_cell(const DevBlock &hb, int i, int j, int k) {
+  return hb.cell0 + plane_row_base(hb.PO, hb.F, hb.mmax, hb.nx, i + j + k, k) + j;
+}
+
+// natural index p = i + nx*(j + ny*k)  ->  record slot `slot` of plan cell
+// (records of `stride` values, FP32 or FP64).
 // zero_face: 0 keep; 1..6 zero the coefficient on the face i=0, i=nx-1,
 // j=0, j=ny-1, k=0, k=nz-1 (an entry that points out of the block).
 // shift_axis: 0 read src[p]; 1/2/3 read src at the lower neighbour along
 // i/j/k (0 on the lower face): builds AW/AS/AB of a symmetric matrix from AE/AN/AT.
-template <typename TO>
-__global__ void k_to_plan(const void *src, int src_is_f32, TO *dst, DevBlock hb, int zero_face,
-                          int shift_axis) {
+__global__ void k_to_records(const void *src, int src_is_f32, void *dst, int dst_is_f32, int stride, int slot,
+                             DevBlock hb, int zero_face, int shift_axis) {
   const long long n = (long long)hb.nx * hb.ny * hb.nz;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
@@ -72,29 +79,34 @@ __global__ void k_to_plan(const void *src, int src_is_f32, TO *dst, DevBlock hb,
     if (shift_axis == 2) { if (j == 0) zero = true; else q = p - hb.nx; }
     if (shift_axis == 3) { if (k == 0) zero = true; else q = p - (long long)hb.nx * hb.ny; }
     double v = 0.0;
-    if (!zero) v = src_is_f32 ? (double)((const float *)src)[q] : ((const double *)src)[q];
-    dst[hb.cell0 + hb.rbT[(long long)k * hb.nplanes + i + j + k] + j] = (TO)v;
+    if (!zero && src) v = src_is_f32 ? (double)((const float *)src)[q] : ((const double *)src)[q];
+    const long long a = plan_cell(hb, i, j, k) * stride + slot;
+    if (dst_is_f32) ((float *)dst)[a] = (float)v;
+    else ((double *)dst)[a] = v;
   }
 }
 
-template <typename TO>
-static cudaError_t to_plan(const void *src, int src_is_f32, TO *dst, const DevBlock &hb, int zf, int sh,
-                           cudaStream_t st) {
-  const long long n = (long long)hb.nx * hb.ny * hb.nz;
-  int grid = (int)((n + 255) / 256);
-  if (grid > 152 * 32) grid = 152 * 32;
-  if (grid < 1) grid = 1;
-  k_to_plan<TO><<<grid, 256, 0, st>>>(src, src_is_f32, dst, hb, zf, sh);
+cudaError_t launch_to_records(const void *src, int src_is_f32, void *dst, int dst_is_f32, int stride, int slot,
+                              const DevBlock &hb, int zf, int sh, cudaStream_t st) {
+  k_to_records<<<util_grid((long long)hb.nx * hb.ny * hb.nz), 256, 0, st>>>(src, src_is_f32, dst, dst_is_f32,
+                                                                            stride, slot, hb, zf, sh);
   return cudaGetLastError();
 }
 
-cudaError_t launch_to_plan_f64(const void *src, int src_is_f32, double *dst, const DevBlock &hb, int zf,
-                               int sh, cudaStream_t st) {
-  return to_plan<double>(src, src_is_f32, dst, hb, zf, sh, st);
+__global__ void k_to_plan(const double *src, double *dst, DevBlock hb) {
+  const long long n = (long long)hb.nx * hb.ny * hb.nz;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(p % hb.nx);
+    const int j = (int)((p / hb.nx) % hb.ny);
+    const int k = (int)(p / ((long long)hb.nx * hb.ny));
+    dst[plan_cell(hb, i, j, k)] = src[p];
+  }
 }
-cudaError_t launch_to_plan_f32(const void *src, int src_is_f32, float *dst, const DevBlock &hb, int zf,
-                               int sh, cudaStream_t st) {
-  return to_plan<float>(src, src_is_f32, dst, hb, zf, sh, st);
+
+cudaError_t launch_to_plan_f64(const double *src, double *dst, const DevBlock &hb, cudaStream_t st) {
+  k_to_plan<<<util_grid((long long)hb.nx * hb.ny * hb.nz), 256, 0, st>>>(src, dst, hb);
+  return cudaGetLastError();
 }
 
 __global__ void k_from_plan(const double *src, double *dst, DevBlock hb) {
@@ -104,55 +116,44 @@ __global__ void k_from_plan(const double *src, double *dst, DevBlock hb) {
     const int i = (int)(p % hb.nx);
     const int j = (int)((p / hb.nx) % hb.ny);
     const int k = (int)(p / ((long long)hb.nx * hb.ny));
-    dst[p] = src[hb.cell0 + hb.rbT[(long long)k * hb.nplanes + i + j + k] + j];
+    dst[p] = src[plan_cell(hb, i, j, k)];
   }
 }
 
 cudaError_t launch_from_plan_f64(const double *src, double *dst, const DevBlock &hb, cudaStream_t st) {
-  const long long n = (long long)hb.nx * hb.ny * hb.nz;
-  int grid = (int)((n + 255) / 256);
-  if (grid > 152 * 32) grid = 152 * 32;
-  if (grid < 1) grid = 1;
-  k_from_plan<<<grid, 256, 0, st>>>(src, dst, hb);
+  k_from_plan<<<util_grid((long long)hb.nx * hb.ny * hb.nz), 256, 0, st>>>(src, dst, hb);
   return cudaGetLastError();
 }
 
-struct Ptr7 { const double *f[7]; double *o[7]; };
-__global__ void k_export7(Ptr7 P, DevBlock hb) {
+struct Out7 { double *o[7]; };
+template <typename TF>
+__global__ void k_export(const TF *recF, const TF *recB, int rsf, Out7 O, DevBlock hb) {
   const long long n = (long long)hb.nx * hb.ny * hb.nz;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(p % hb.nx);
     const int j = (int)((p / hb.nx) % hb.ny);
     const int k = (int)(p / ((long long)hb.nx * hb.ny));
-    const long long a = hb.cell0 + hb.rbT[(long long)k * hb.nplanes + i + j + k] + j;
-#pragma unroll
-    for (int q = 0; q < 7; ++q) P.o[q][p] = P.f[q][a];
+    const long long a = plan_cell(hb, i, j, k);
+    const TF *f = recF + a * rsf;
+    const TF *b = recB + a * 4;
+    O.o[0][p] = (double)f[REC_LB];
+    O.o[1][p] = (double)f[REC_LW];
+    O.o[2][p] = (double)f[REC_LS];
+    O.o[3][p] = (double)f[REC_RLP];
+    O.o[4][p] = (double)b[RECB_UN];
+    O.o[5][p] = (double)b[RECB_UE];
+    O.o[6][p] = (double)b[RECB_UT];
   }
 }
 
-cudaError_t launch_plan_to_natural_factors(const double *const f[7], double *const out[7], const DevBlock &hb,
-                                           cudaStream_t st) {
-  Ptr7 P;
-  for (int q = 0; q < 7; ++q) { P.f[q] = f[q]; P.o[q] = out[q]; }
-  const long long n = (long long)hb.nx * hb.ny * hb.nz;
-  int grid = (int)((n + 255) / 256);
-  if (grid > 152 * 32) grid = 152 * 32;
-  if (grid < 1) grid = 1;
-  k_export7<<<grid, 256, 0, st>>>(P, hb);
-  return cudaGetLastError();
-}
-
-__global__ void k_f64_to_f32(const double *src, float *dst, long long n) {
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-       p += (long long)gridDim.x * blockDim.x)
-    dst[p] = (float)src[p];
-}
-cudaError_t launch_f64_to_f32(const double *src, float *dst, long long n, cudaStream_t st) {
-  int grid = (int)((n + 255) / 256);
-  if (grid > 152 * 32) grid = 152 * 32;
-  if (grid < 1) grid = 1;
-  k_f64_to_f32<<<grid, 256, 0, st>>>(src, dst, n);
+cudaError_t launch_export_factors(const void *recF, const void *recB, int is_f32, int rsf, double *const out[7],
+                                  const DevBlock &hb, cudaStream_t st) {
+  Out7 O;
+  for (int q = 0; q < 7; ++q) O.o[q] = out[q];
+  const int g = util_grid((long long)hb.nx * hb.ny * hb.nz);
+  if (is_f32) k_export<float><<<g, 256, 0, st>>>((const float *)recF, (const float *)recB, rsf, O, hb);
+  else k_export<double><<<g, 256, 0, st>>>((const double *)recF, (const double *)recB, rsf, O, hb);
   return cudaGetLastError();
 }
 
