@@ -155,6 +155,19 @@ int sip_export_factors(sip_plan *plan, int blk, double *const out[7]);
  * ascends within a row.  Entries of empty rows are INT32_MIN. */
 int sip_plane_layout(int nx, int ny, int nz, int32_t *rbT);
 
+/* ||b - A x||_2 (*rnorm_out) and ||b||_2 (*bnorm_out) of one block, computed
+ * directly on the descriptor's natural-layout arrays (the residual of
+ * resforward3d, Sec. 4.1 / Table 1, without a plan): FP64 arithmetic (FP32
+ * coefficients are widened), sums in a fixed order that depends only on N,
+ * so results are bitwise reproducible.  Coefficients that point outside the
+ * block are ignored; symmetric != 0 reads AW/AS/AB as AE(W)/AN(S)/AT(B).
+ * Only blk->ap..at, b, x, dims, coef_dtype and symmetric are read; nothing is
+ * written but the outputs.  rnorm_out, bnorm_out: host, nullable.  Allocates
+ * and frees 16 bytes of device scratch per 4096 cells for the call and
+ * synchronises the context's stream.  Errors: SIP_ERR_INVALID_ARG (bad
+ * descriptor), SIP_ERR_OOM, SIP_ERR_CUDA. */
+int sip_residual_norm(sip_ctx *ctx, const sip_block_desc *blk, double *rnorm_out, double *bnorm_out);
+
 /* Measurement aids.  sip_profile_enable(plan, 1) records a CUDA event pair
  * on the plan's stream around every later kernel launch of the plan;
  * sip_profile_read synchronises the stream and writes, for each kernel kind

@@ -850,6 +850,48 @@ int sip_plane_layout(int nx, int ny, int nz, int32_t *rbT) {
   return SIP_OK;
 }
 
+// Natural-layout view of a block descriptor for the residual norm; "" or the
+// reason the descriptor is unusable.
+static std::string natblock_from_desc(const sip_block_desc *d, NatBlock *nb) {
+  if (!d) return "null block descriptor";
+  if (d->nx < 1 || d->ny < 1 || d->nz < 1) return "block dims must be >= 1";
+  if ((long long)d->nx * d->ny * d->nz >= (1ll << 31)) return "block too large (nx*ny*nz must be < 2^31)";
+  if (d->coef_dtype != 0 && d->coef_dtype != 1) return "coef_dtype must be 0 or 1";
+  if (!d->ap || !d->ae || !d->an || !d->at || !d->b || !d->x) return "null coefficient, rhs or solution pointer";
+  if (!d->symmetric && (!d->aw || !d->as || !d->ab)) return "aw/as/ab may be NULL only for symmetric blocks";
+  nb->nx = d->nx;
+  nb->ny = d->ny;
+  nb->nz = d->nz;
+  nb->coef_f32 = d->coef_dtype;
+  nb->symmetric = d->symmetric != 0;
+  const void *a[7] = {d->ap, d->aw, d->ae, d->as, d->an, d->ab, d->at};
+  for (int q = 0; q < 7; ++q) nb->a[q] = a[q];
+  nb->b = d->b;
+  nb->x = d->x;
+  return "";
+}
+
+int sip_residual_norm(sip_ctx *ctx, const sip_block_desc *blk, double *rnorm_out, double *bnorm_out) {
+  if (!ctx) return SIP_ERR_INVALID_ARG;
+  NatBlock nb;
+  const std::string why = natblock_from_desc(blk, &nb);
+  if (!why.empty()) return fail(ctx, SIP_ERR_INVALID_ARG, why);
+  CU(cudaSetDevice(ctx->device));
+  const long long np = resnorm_parts(nb);
+  double *scratch = nullptr;
+  CU(cudaMalloc(&scratch, (size_t)(2 * np + 2) * sizeof(double)));
+  double out[2] = {0.0, 0.0};
+  cudaError_t e = launch_resnorm(nb, scratch, scratch + 2 * np, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, scratch + 2 * np, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(scratch);
+  if (e != cudaSuccess) return fail(ctx, SIP_ERR_CUDA, std::string("residual norm: ") + cudaGetErrorString(e));
+  if (rnorm_out) *rnorm_out = out[0];
+  if (bnorm_out) *bnorm_out = out[1];
+  return SIP_OK;
+}
+
 int sip_profile_enable(sip_plan *p, int enable) {
   if (!p) return SIP_ERR_INVALID_ARG;
   p->prof = enable != 0;

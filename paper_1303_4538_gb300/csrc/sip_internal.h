@@ -149,6 +149,21 @@ cudaError_t launch_set_ctl(Ctl *ctl, double rtol, int max_iters, cudaStream_t st
 cudaError_t launch_export_factors(const void *recF, const void *recB, int is_f32, int rsf,
                                   double *const out[7], const DevBlock &hb, cudaStream_t st);
 
+// Natural-layout block for the residual norm (sip_resnorm.cu).  a[] = AP, AW,
+// AE, AS, AN, AB, AT (double or float); symmetric: AW/AS/AB are not read.
+struct NatBlock {
+  int nx, ny, nz;
+  int coef_f32;
+  int symmetric;
+  const void *a[7];
+  const double *b, *x;
+};
+constexpr int kResChunk = 4096;  // cells per partial pair of the residual norm
+// number of partial pairs (2 doubles each) the residual norm of nb needs
+long long resnorm_parts(const NatBlock &nb);
+// ||b - A x||_2, ||b||_2 of nb into out2[0..1] (device); scratch: 2 * resnorm_parts(nb) doubles
+cudaError_t launch_resnorm(const NatBlock &nb, double *scratch, double *out2, cudaStream_t st);
+
 // finalize modes
 constexpr int FIN_BNORM = 0;   // partials are ||b||^2 pieces: set ctl->bnorm
 constexpr int FIN_RELRES = 1;  // partials are ||r||^2 pieces: relres, stop rule, counters

@@ -41,7 +41,7 @@ EXPORTED = (
     "sip_default_options", "sip_create", "sip_destroy", "sip_last_error", "sip_factor",
     "sip_iterate", "sip_solve", "sip_get_history", "sip_export_factors", "sip_plan_bytes",
     "sip_plan_destroy", "sip_plane_layout", "sip_profile_enable", "sip_profile_read",
-    "sip_launch_count", "sip_kernel_name",
+    "sip_launch_count", "sip_kernel_name", "sip_residual_norm",
 )
 
 
@@ -108,6 +108,7 @@ def lib():
         L.sip_profile_read.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int64), I]
         L.sip_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
         L.sip_kernel_name.argtypes = [I]
+        L.sip_residual_norm.argtypes = [P, ctypes.POINTER(sip_block_desc), ctypes.POINTER(D), ctypes.POINTER(D)]
         L.sip_kernel_name.restype = ctypes.c_char_p
         for name in EXPORTED:
             if name not in ("sip_default_options", "sip_last_error", "sip_kernel_name"):
@@ -145,6 +146,13 @@ class Context:
         if rc == SIP_OK or (allow_not_converged and rc == SIP_NOT_CONVERGED):
             return rc
         raise SipError(rc, lib().sip_last_error(self.h).decode())
+
+    def residual_norm(self, desc: "sip_block_desc"):
+        """sip_residual_norm: (||b - A x||_2, ||b||_2) of one block descriptor."""
+        r = ctypes.c_double(0.0)
+        b = ctypes.c_double(0.0)
+        self.check(lib().sip_residual_norm(self.h, ctypes.byref(desc), ctypes.byref(r), ctypes.byref(b)))
+        return r.value, b.value
 
     def close(self):
         if self.h:
