@@ -168,6 +168,25 @@ int sip_plane_layout(int nx, int ny, int nz, int32_t *rbT);
  * descriptor), SIP_ERR_OOM, SIP_ERR_CUDA. */
 int sip_residual_norm(sip_ctx *ctx, const sip_block_desc *blk, double *rnorm_out, double *bnorm_out);
 
+/* Allocation-free variant of sip_residual_norm (this library's addition; the
+ * paper has no counterpart).  Same arithmetic, chunking and summation order,
+ * so the same bits, but:
+ *   - norms_dev (device, 2 doubles, 8-byte aligned, must not overlap the
+ *     block's arrays) receives ||b - A x||_2 and ||b||_2 in stream order; the
+ *     call neither synchronises nor copies to the host;
+ *   - no device memory is allocated or freed: the partial sums live in one
+ *     fixed 256 KiB array of the library per device, so blocks are limited to
+ *     SIP_NOALLOC_MAX_CELLS cells (larger: SIP_ERR_INVALID_ARG, nothing
+ *     launched).  No part of that array needs to start at zero;
+ *   - calls whose work may overlap on one device (other streams, contexts or
+ *     threads) race on that array: the caller must order them;
+ *   - the first call on each device looks the array's address up (and may
+ *     load the library's device code); make it before any stream capture
+ *     begins and outside time-critical code.
+ * Errors: SIP_ERR_INVALID_ARG, SIP_ERR_CUDA. */
+#define SIP_NOALLOC_MAX_CELLS 67108864LL
+int sip_residual_norm_noalloc(sip_ctx *ctx, const sip_block_desc *blk, double *norms_dev);
+
 /* Measurement aids.  sip_profile_enable(plan, 1) records a CUDA event pair
  * on the plan's stream around every later kernel launch of the plan;
  * sip_profile_read synchronises the stream and writes, for each kernel kind

@@ -892,6 +892,25 @@ int sip_residual_norm(sip_ctx *ctx, const sip_block_desc *blk, double *rnorm_out
   return SIP_OK;
 }
 
+int sip_residual_norm_noalloc(sip_ctx *ctx, const sip_block_desc *blk, double *norms_dev) {
+  if (!ctx) return SIP_ERR_INVALID_ARG;
+  if (!norms_dev) return fail(ctx, SIP_ERR_INVALID_ARG, "null output pointer");
+  NatBlock nb;
+  const std::string why = natblock_from_desc(blk, &nb);
+  if (!why.empty()) return fail(ctx, SIP_ERR_INVALID_ARG, why);
+  const long long np = resnorm_parts(nb);
+  if (np > kNoallocParts)
+    return fail(ctx, SIP_ERR_INVALID_ARG,
+                "block has " + std::to_string((long long)nb.nx * nb.ny * nb.nz) +
+                    " cells; sip_residual_norm_noalloc handles at most " +
+                    std::to_string((long long)kNoallocParts * kResChunk) + " (SIP_NOALLOC_MAX_CELLS)");
+  CU(cudaSetDevice(ctx->device));
+  double *scratch = nullptr;
+  CU(noalloc_scratch(ctx->device, &scratch));
+  CU(launch_resnorm(nb, scratch, norms_dev, ctx->stream));
+  return SIP_OK;
+}
+
 int sip_profile_enable(sip_plan *p, int enable) {
   if (!p) return SIP_ERR_INVALID_ARG;
   p->prof = enable != 0;

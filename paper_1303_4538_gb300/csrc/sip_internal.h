@@ -163,6 +163,12 @@ constexpr int kResChunk = 4096;  // cells per partial pair of the residual norm
 long long resnorm_parts(const NatBlock &nb);
 // ||b - A x||_2, ||b||_2 of nb into out2[0..1] (device); scratch: 2 * resnorm_parts(nb) doubles
 cudaError_t launch_resnorm(const NatBlock &nb, double *scratch, double *out2, cudaStream_t st);
+// fixed scratch of the allocation-free residual norm (sip_noalloc.cu): room for
+// kNoallocParts partial pairs; its device address for `device` (which must be
+// current) is resolved once and cached
+constexpr int kNoallocParts = 16384;
+constexpr int kNoallocMaxDevices = 64;
+cudaError_t noalloc_scratch(int device, double **out);
 
 // finalize modes
 constexpr int FIN_BNORM = 0;   // partials are ||b||^2 pieces: set ctl->bnorm

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libsip.so")
 SIP_OK = 0
 SIP_NOT_CONVERGED = 1
 SIP_ERR_INVALID_ARG = -1
+SIP_NOALLOC_MAX_CELLS = 67108864  # include/sip.h
 SIP_ERR_NO_DEVICE = -2
 SIP_ERR_CUDA = -3
 SIP_ERR_OOM = -4
@@ -42,6 +43,7 @@ EXPORTED = (
     "sip_iterate", "sip_solve", "sip_get_history", "sip_export_factors", "sip_plan_bytes",
     "sip_plan_destroy", "sip_plane_layout", "sip_profile_enable", "sip_profile_read",
     "sip_launch_count", "sip_kernel_name", "sip_residual_norm",
+    "sip_residual_norm_noalloc",
 )
 
 
@@ -109,6 +111,7 @@ def lib():
         L.sip_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
         L.sip_kernel_name.argtypes = [I]
         L.sip_residual_norm.argtypes = [P, ctypes.POINTER(sip_block_desc), ctypes.POINTER(D), ctypes.POINTER(D)]
+        L.sip_residual_norm_noalloc.argtypes = [P, ctypes.POINTER(sip_block_desc), P]
         L.sip_kernel_name.restype = ctypes.c_char_p
         for name in EXPORTED:
             if name not in ("sip_default_options", "sip_last_error", "sip_kernel_name"):
@@ -153,6 +156,11 @@ class Context:
         b = ctypes.c_double(0.0)
         self.check(lib().sip_residual_norm(self.h, ctypes.byref(desc), ctypes.byref(r), ctypes.byref(b)))
         return r.value, b.value
+
+    def residual_norm_noalloc(self, desc: "sip_block_desc", out) -> None:
+        """sip_residual_norm_noalloc: writes (||b - A x||_2, ||b||_2) into the
+        device array `out` (2 doubles) in stream order; no allocation, no sync."""
+        self.check(lib().sip_residual_norm_noalloc(self.h, ctypes.byref(desc), ctypes.c_void_p(_ptr(out))))
 
     def close(self):
         if self.h:
