@@ -133,10 +133,15 @@ class ClockSampler:
         return out
 
 
+SWEEP_SOURCES = ("sip_sweeps.cuh", "sip_layout.h", "sip_k32.cu", "sip_k64.cu", "sip_kres.cu")
+
+
 def src_hash() -> str:
+    """Hash of the sources that define the sweep kernels (their DRAM traffic
+    counters stay valid while these files are unchanged)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1303_4538_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in SWEEP_SOURCES:
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
