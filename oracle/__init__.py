@@ -65,6 +65,8 @@ def lib():
         L.oracle_iterate_f32.restype = None
         L.oracle_solve_refined.argtypes = [I, I, I] + [P] * 23 + [D, I, I, P, P]
         L.oracle_solve_refined.restype = I
+        L.oracle_solve_mb.argtypes = [I, P, P, P, P, P, I, P, I, D, I, P, P]
+        L.oracle_solve_mb.restype = I
         _lib = L
     return _lib
 
@@ -199,6 +201,30 @@ def solve_refined(nx, ny, nz, coefs64, coefs32, factors32, b, x0=None, rtol=1e-8
                                     *[_p(f) for f in F], _p(b), _p(x), float(rtol), int(max_outer),
                                     int(m_inner), _p(hist), ctypes.byref(rel))
     return x, it, rel.value, hist[: it + 1].copy()
+
+
+def solve_multiblock(blocks, ifaces, factors, x0=None, rtol=1e-8, max_iters=100, symmetric=False):
+    """Lagged block-Jacobi SIP over blocks coupled across x interfaces.
+
+    blocks: list of (nx, ny, nz, coefs, b); ifaces: list of (lo, hi, nj, nk);
+    factors: per block the 7 FP64 factor arrays (oracle.factor); x0: list of
+    per-block initial guesses (default zeros).  Returns (xs, n, relres, hist)."""
+    nb = len(blocks)
+    dims = np.array([[bl[0], bl[1], bl[2]] for bl in blocks], dtype=np.int32).reshape(-1)
+    A = [_coefs(bl[3]) for bl in blocks]
+    F = [[_f64(f) for f in fs] for fs in factors]
+    B = [_f64(bl[4]) for bl in blocks]
+    X = [np.zeros(bl[0] * bl[1] * bl[2]) if x0 is None else _f64(x0[i]).copy() for i, bl in enumerate(blocks)]
+    Pa = (ctypes.c_void_p * (7 * nb))(*[a.ctypes.data for arrs in A for a in arrs])
+    Pf = (ctypes.c_void_p * (7 * nb))(*[f.ctypes.data for fs in F for f in fs])
+    Pb = (ctypes.c_void_p * nb)(*[b.ctypes.data for b in B])
+    Px = (ctypes.c_void_p * nb)(*[x.ctypes.data for x in X])
+    ifc = np.array([list(q) for q in ifaces], dtype=np.int32).reshape(-1) if ifaces else np.zeros(4, np.int32)
+    hist = np.zeros(max_iters + 1)
+    rel = ctypes.c_double(0.0)
+    it = lib().oracle_solve_mb(nb, _p(dims), Pa, Pf, Pb, Px, len(ifaces), _p(ifc), 1 if symmetric else 0,
+                               float(rtol), int(max_iters), _p(hist), ctypes.byref(rel))
+    return X, it, rel.value, hist[: it + 1].copy()
 
 
 def norm2(v) -> float:

@@ -370,3 +370,94 @@ int oracle_solve_refined(int nx, int ny, int nz,
   if (relres_out) *relres_out = rel;
   return it;
 }
+
+/* ------------------------------------------------------------------ */
+/* Several blocks coupled across x interfaces (the paper's block-structured
+ * mesh, Sec. 1; blocks exchange boundary data, Sec. 4.2).  Reading: lagged
+ * block Jacobi -- every block relaxes with its own factors and with the
+ * neighbour values of the previous exchange.
+ *
+ * Block b: dims[3b..3b+2] = nx, ny, nz; A[7b+q] = ap, aw, ae, as, an, ab, at;
+ * F[7b+q] = lb, lw, ls, lp, un, ue, ut (its own factorisation); B[b] rhs;
+ * X[b] solution (in: x0, out: x_n).  Interface q: ifc[4q..4q+3] = lo, hi,
+ * nj, nk: cell (nx_lo - 1, j, k) of block lo and cell (0, j, k) of block hi
+ * are neighbours for j < nj, k < nk; the coupling entries are lo's AE there
+ * and hi's AW there (sym != 0: hi's entry is lo's AE, the matrix being
+ * symmetric).
+ *
+ * Iteration: with every block's current x,
+ *   beff_b = b_b - sum over the interfaces of b of (entry) * x_neighbour
+ *   r_b    = beff_b - A_b x_b  (A_b: the block's own entries; an entry that
+ *            points outside the block is not used)
+ * is the residual of the whole coupled system; relres = sqrt(sum_b ||r_b||^2)
+ * / sqrt(sum_b ||b_b||^2) with the stop rule of oracle_solve; otherwise every
+ * block applies y = L^-1 r_b, d = U^-1 y, x_b += d.  Returns n; hist
+ * (nullable, max_iters + 1) gets relres(x_0..x_n). */
+int oracle_solve_mb(int nb, const int *dims, const double *const *A, const double *const *F,
+                    const double *const *B, double *const *X, int nif, const int *ifc, int sym,
+                    double rtol, int max_iters, double *hist, double *relres_out) {
+  size_t nmax = 0;
+  for (int b = 0; b < nb; ++b) {
+    size_t n = (size_t)dims[3 * b] * dims[3 * b + 1] * dims[3 * b + 2];
+    if (n > nmax) nmax = n;
+  }
+  double **beff = (double **)malloc(sizeof(double *) * nb);
+  double **r = (double **)malloc(sizeof(double *) * nb);
+  double *y = (double *)malloc(nmax * sizeof(double));
+  double *d = (double *)malloc(nmax * sizeof(double));
+  nsum bsum = {0.0, 0.0};
+  for (int b = 0; b < nb; ++b) {
+    size_t n = (size_t)dims[3 * b] * dims[3 * b + 1] * dims[3 * b + 2];
+    beff[b] = (double *)malloc(n * sizeof(double));
+    r[b] = (double *)malloc(n * sizeof(double));
+    nsum_add(&bsum, oracle_dot_sq((int64_t)n, B[b]));
+  }
+  double bb = sqrt(nsum_get(&bsum));
+  double scale = bb > 0.0 ? bb : 1.0;
+  int it = 0;
+  double rel = 0.0;
+  for (;;) {
+    for (int b = 0; b < nb; ++b) {
+      size_t n = (size_t)dims[3 * b] * dims[3 * b + 1] * dims[3 * b + 2];
+      memcpy(beff[b], B[b], n * sizeof(double));
+    }
+    for (int q = 0; q < nif; ++q) {
+      int lo = ifc[4 * q], hi = ifc[4 * q + 1], nj = ifc[4 * q + 2], nk = ifc[4 * q + 3];
+      int nxl = dims[3 * lo], nyl = dims[3 * lo + 1];
+      int nxh = dims[3 * hi], nyh = dims[3 * hi + 1];
+      const double *ae_lo = A[7 * lo + 2];
+      const double *aw_hi = sym ? NULL : A[7 * hi + 1];
+      for (int k = 0; k < nk; ++k)
+        for (int j = 0; j < nj; ++j) {
+          size_t pl = (size_t)(nxl - 1) + (size_t)nxl * ((size_t)j + (size_t)nyl * k);
+          size_t ph = (size_t)nxh * ((size_t)j + (size_t)nyh * k);
+          double elo = ae_lo[pl];
+          double ehi = sym ? elo : aw_hi[ph];
+          beff[lo][pl] -= elo * X[hi][ph];
+          beff[hi][ph] -= ehi * X[lo][pl];
+        }
+    }
+    nsum rs = {0.0, 0.0};
+    for (int b = 0; b < nb; ++b) {
+      int nx = dims[3 * b], ny = dims[3 * b + 1], nz = dims[3 * b + 2];
+      const double *const *a = A + 7 * b;
+      nsum_add(&rs, oracle_residual(nx, ny, nz, a[0], a[1], a[2], a[3], a[4], a[5], a[6], beff[b], X[b], r[b]));
+    }
+    rel = sqrt(nsum_get(&rs)) / scale;
+    if (hist) hist[it] = rel;
+    if (rel <= rtol || it >= max_iters) break;
+    for (int b = 0; b < nb; ++b) {
+      int nx = dims[3 * b], ny = dims[3 * b + 1], nz = dims[3 * b + 2];
+      size_t n = (size_t)nx * ny * nz;
+      const double *const *f = F + 7 * b;
+      oracle_forward(nx, ny, nz, f[0], f[1], f[2], f[3], r[b], y);
+      oracle_backward(nx, ny, nz, f[4], f[5], f[6], y, d);
+      for (size_t p = 0; p < n; ++p) X[b][p] += d[p];
+    }
+    ++it;
+  }
+  for (int b = 0; b < nb; ++b) { free(beff[b]); free(r[b]); }
+  free(beff); free(r); free(y); free(d);
+  if (relres_out) *relres_out = rel;
+  return it;
+}

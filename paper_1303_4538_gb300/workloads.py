@@ -151,6 +151,66 @@ def convdiff_pe10_384cube(n: int = 384) -> Block:
     return make_block(n, n, n, seed=4542, kind="convdiff", pe=10.0)
 
 
+@dataclass
+class Mesh:
+    """Blocks of a block-structured mesh chained along x: interface q =
+    (lo, hi, nj, nk) joins cell (nx_lo - 1, j, k) of block lo with cell
+    (0, j, k) of block hi for j < nj, k < nk.  The coupling entries sit in
+    lo's AE and hi's AW on those cells; b of every block includes the
+    interface terms of the manufactured solution."""
+
+    blocks: List[Block]
+    ifaces: List[Tuple[int, int, int, int]]
+
+    @property
+    def n(self) -> int:
+        return sum(b.n for b in self.blocks)
+
+
+def make_mesh(dims, seed: int, kind: str = "convdiff", pe: Optional[float] = None) -> Mesh:
+    """Blocks of sizes dims[b] = (nx, ny, nz), block b drawn with
+    make_block(seed = seed * 1000 + b); consecutive blocks coupled across the
+    overlap rectangle of their x faces, nj = min(ny), nk = min(nz).  Each
+    interface face draws its conductance D ~ U[0.5, 2] (and, for convdiff, a
+    flux as make_block does) from Generator(PCG64([seed, 1])) in interface
+    order; the two upwind entries go to lo's AE and hi's AW and their
+    magnitudes to the two cells' AP; b = A x* of the coupled system."""
+    dims = [tuple(int(v) for v in d) for d in dims]
+    blocks = [make_block(nx, ny, nz, seed=seed * 1000 + b, kind=kind, pe=pe) for b, (nx, ny, nz) in enumerate(dims)]
+    rng = np.random.Generator(np.random.PCG64([seed, 1]))
+    ifaces = []
+    for lo in range(len(blocks) - 1):
+        hi = lo + 1
+        L, H = blocks[lo], blocks[hi]
+        nj, nk = min(L.ny, H.ny), min(L.nz, H.nz)
+        D = rng.uniform(0.5, 2.0, size=(nk, nj))
+        if kind == "convdiff":
+            g = rng.standard_normal(size=(nk, nj))
+            F = g if pe is None else (pe / 0.6745) * D * g
+        else:
+            F = np.zeros((nk, nj))
+        kk, jj = np.meshgrid(np.arange(nk), np.arange(nj), indexing="ij")
+        pl = (L.nx - 1) + L.nx * (jj + L.ny * kk)
+        ph = H.nx * (jj + H.ny * kk)
+        e_lo = -(D + np.maximum(-F, 0.0))
+        e_hi = -(D + np.maximum(F, 0.0))
+        L.coefs["ae"][pl] = e_lo
+        H.coefs["aw"][ph] = e_hi
+        L.coefs["ap"][pl] += np.abs(e_lo)
+        H.coefs["ap"][ph] += np.abs(e_hi)
+        ifaces.append((lo, hi, nj, nk))
+    for b, B in enumerate(blocks):
+        B.b = apply_matrix(B.nx, B.ny, B.nz, B.coefs, B.xstar)
+    for lo, hi, nj, nk in ifaces:
+        L, H = blocks[lo], blocks[hi]
+        kk, jj = np.meshgrid(np.arange(nk), np.arange(nj), indexing="ij")
+        pl = ((L.nx - 1) + L.nx * (jj + L.ny * kk)).reshape(-1)
+        ph = (H.nx * (jj + H.ny * kk)).reshape(-1)
+        L.b[pl] += L.coefs["ae"][pl] * H.xstar[ph]
+        H.b[ph] += H.coefs["aw"][ph] * L.xstar[pl]
+    return Mesh(blocks, ifaces)
+
+
 def random_block_dims(rng: np.random.Generator, count: int, lo: int, hi: int) -> np.ndarray:
     return rng.integers(lo, hi + 1, size=(count, 3))
 
@@ -168,3 +228,9 @@ def batched_mesh_dims(seed: int = 4541, nblocks: int = 64, lo: int = 24, hi: int
         if total_lo <= tot <= total_hi:
             return dims, t
     raise RuntimeError("no admissible draw")
+
+
+def batched_mesh(seed: int = 4541) -> Mesh:
+    """The 64-block convection-diffusion mesh of ~20 M cells (x chain)."""
+    dims, _ = batched_mesh_dims(seed)
+    return make_mesh(dims, seed, kind="convdiff")
