@@ -51,7 +51,9 @@
  * L U = A + N, by alpha = 0 (ILU(0)) and by the 1-D case (exact LU); the
  * iteration by the dense preconditioned-Richardson step and by convergence to
  * the dense solution; the single-precision and refinement drivers by
- * convergence to the FP64 solution.  No value printed in the paper can be
+ * convergence to the FP64 solution; the multi-block solve by the dense
+ * global residual, the dense block-Jacobi Richardson step and convergence to
+ * the dense global solution on tiny meshes.  No value printed in the paper can be
  * matched (it prints none for SIP).
  */
 #include <math.h>
