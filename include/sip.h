@@ -85,8 +85,13 @@ typedef struct {
  * Sec. 1; exchange at block boundaries, Sec. 4.2): the +x face of blk_lo touches
  * the -x face of blk_hi on the rectangle j < nj, k < nk (both anchored at
  * j = k = 0).  Across it, blk_lo's AE at i = nx-1 and blk_hi's AW at i = 0
- * couple the two blocks; the coupling enters each block's residual with the
- * neighbour's values from the previous iteration (lagged, block Jacobi). */
+ * (for symmetric blocks: blk_lo's AE on both sides) couple the two blocks;
+ * the coupling enters each block's residual with the neighbour's values from
+ * the previous iteration (lagged, block Jacobi), so relres and the stop rule
+ * refer to the coupled system while each block relaxes with its own factors.
+ * Rules: 0 <= blk_lo, blk_hi < nblocks, blk_lo != blk_hi; 1 <= nj <= both
+ * blocks' ny, 1 <= nk <= both blocks' nz; each block face carries at most one
+ * interface.  Otherwise sip_factor returns SIP_ERR_INVALID_ARG. */
 typedef struct {
   int32_t blk_lo, blk_hi;
   int32_t nj, nk;

@@ -128,6 +128,12 @@ struct sip_plan {
   // <file> when the plan is destroyed
   unsigned long long *trace = nullptr;
   std::string trace_path;
+  // multi-block interfaces: lagged coupling terms folded into beff64 (the
+  // right-hand side the residual kernels read) before every iteration
+  std::vector<sip_interface> ifaces;
+  double *beff64 = nullptr;
+  HaloEntry *halo = nullptr;
+  int nhalo = 0;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -257,13 +263,21 @@ int check_status(sip_plan *p) {
 }
 
 // Forward + finalize + backward of one FP64 iteration.
+// Interface terms of the coupled residual from the current x (lagged block Jacobi).
+int enqueue_halo(sip_plan *p) {
+  sip_ctx *ctx = p->ctx;
+  if (p->nhalo > 0) UTIL(launch_halo(p->halo, p->nhalo, p->b64, p->x64, p->beff64, p->ctl, ctx->stream));
+  return SIP_OK;
+}
+
 int enqueue_iter_f64(sip_plan *p) {
   sip_ctx *ctx = p->ctx;
+  if (int rc = enqueue_halo(p)) return rc;
   FwdParams<double> f;
   f.c = common(p, false, 0, 1, 0, p->sym ? K_FWD64S : K_FWD64);
   f.rec = (const double *)p->recF;
   f.rsf = p->rsf;
-  f.b = p->b64;
+  f.b = p->beff64 ? p->beff64 : p->b64;
   f.x = p->x64;
   f.y = p->y64;
   f.partials = p->partials;
@@ -284,13 +298,15 @@ int enqueue_iter_f64(sip_plan *p) {
 int enqueue_iter_refined(sip_plan *p) {
   sip_ctx *ctx = p->ctx;
   const int m = std::max(1, p->opt.inner_iters);
+  if (int rc = enqueue_halo(p)) return rc;
+  const double *bres = p->beff64 ? p->beff64 : p->b64;
   if (p->a32in) {
     ResParams<float> r;
     r.blocks = p->d_blocks; r.tiles = p->d_tiles_f; r.ntiles = p->ntiles; r.tab_ints = p->tab_ints;
     r.ctl = p->ctl; r.status = p->status;
     r.arec = (const float *)p->recF + 4;
     r.astride = p->rsf;
-    r.b = p->b64; r.x = p->x64; r.r32 = p->r32; r.partials = p->partials;
+    r.b = bres; r.x = p->x64; r.r32 = p->r32; r.partials = p->partials;
     CU(launch(p, p->sym ? K_RES32AS : K_RES32A, r));
   } else {
     ResParams<double> r;
@@ -298,7 +314,7 @@ int enqueue_iter_refined(sip_plan *p) {
     r.ctl = p->ctl; r.status = p->status;
     r.arec = p->arec64;
     r.astride = p->sym ? 4 : 8;
-    r.b = p->b64; r.x = p->x64; r.r32 = p->r32; r.partials = p->partials;
+    r.b = bres; r.x = p->x64; r.r32 = p->r32; r.partials = p->partials;
     CU(launch(p, p->sym ? K_RES64S : K_RES64, r));
   }
   UTIL(launch_finalize(p->partials, p->ntiles, p->ctl, p->hist, p->hist_cap, p->status, FIN_RELRES, ctx->stream));
@@ -334,6 +350,9 @@ int begin_sequence(sip_plan *p, double rtol, int max_iters) {
     UTIL(launch_to_plan_f64(bh.d.b, p->b64, bh.db, ctx->stream));
     UTIL(launch_to_plan_f64(bh.d.x, p->x64, bh.db, ctx->stream));
   }
+  if (p->beff64)
+    CU(cudaMemcpyAsync(p->beff64, p->b64, (size_t)p->ncells * sizeof(double), cudaMemcpyDeviceToDevice,
+                       ctx->stream));
   UTIL(launch_sumsq_partials(p->b64, p->ncells, p->bparts, p->nbparts, ctx->stream));
   UTIL(launch_finalize(p->bparts, p->nbparts, p->ctl, p->hist, p->hist_cap, p->status, FIN_BNORM, ctx->stream));
   return SIP_OK;
@@ -482,7 +501,6 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
   *out = nullptr;
   if (!blocks || nblocks < 1) return fail(ctx, SIP_ERR_INVALID_ARG, "need at least one block");
   if (nifaces < 0 || (nifaces > 0 && !ifaces)) return fail(ctx, SIP_ERR_INVALID_ARG, "bad interface list");
-  if (nifaces > 0) return fail(ctx, SIP_ERR_INVALID_ARG, "interfaces are not supported by this build yet");
   sip_options opt;
   if (opt_in) opt = *opt_in;
   else sip_default_options(&opt);
@@ -510,6 +528,20 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     ncells += n;
   }
   if (ncells >= (1ll << 31)) return fail(ctx, SIP_ERR_INVALID_ARG, "plan too large (total cells must be < 2^31)");
+  {
+    std::vector<int> east(nblocks, 0), west(nblocks, 0);
+    for (int q = 0; q < nifaces; ++q) {
+      const sip_interface &f = ifaces[q];
+      const std::string tag = "interface " + std::to_string(q) + ": ";
+      if (f.blk_lo < 0 || f.blk_lo >= nblocks || f.blk_hi < 0 || f.blk_hi >= nblocks || f.blk_lo == f.blk_hi)
+        return fail(ctx, SIP_ERR_INVALID_ARG, tag + "block indices out of range or equal");
+      const sip_block_desc &L = blocks[f.blk_lo], &H = blocks[f.blk_hi];
+      if (f.nj < 1 || f.nk < 1 || f.nj > std::min(L.ny, H.ny) || f.nk > std::min(L.nz, H.nz))
+        return fail(ctx, SIP_ERR_INVALID_ARG, tag + "overlap rectangle must lie inside both x faces");
+      if (east[f.blk_lo]++ || west[f.blk_hi]++)
+        return fail(ctx, SIP_ERR_INVALID_ARG, tag + "a block face carries at most one interface");
+    }
+  }
   if (opt.tile_j != 0 && opt.tile_j != kTJ) return fail(ctx, SIP_ERR_INVALID_ARG, "tile_j must be 0 or 32");
   if (opt.tile_k < 0 || opt.tile_k > 64 || (opt.tile_k > 0 && opt.tile_k % 2 != 0))
     return fail(ctx, SIP_ERR_INVALID_ARG, "tile_k must be 0 (auto) or an even number <= 64");
@@ -524,6 +556,7 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
   p->a32in = blocks[0].coef_dtype == 1;
   p->ncells = ncells;
   p->blocks.resize(nblocks);
+  p->ifaces.assign(ifaces, ifaces + nifaces);
   for (int b = 0; b < nblocks; ++b) {
     BlockHost &bh = p->blocks[b];
     bh.d = blocks[b];
@@ -648,6 +681,53 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     if (e != cudaSuccess) return bail(e, "pinned control block");
   }
   cudaStream_t st = ctx->stream;
+  std::vector<HaloEntry> hents;
+  std::vector<HaloSrc> hsrcs;
+  if (nifaces > 0) {
+    // one entry per interface face cell, couplings in interface order (lo side first)
+    std::vector<int> at_cell;  // entry of a plan cell, -1 if none
+    at_cell.assign((size_t)ncells, -1);
+    auto cell_of = [&](int b, int i, int j, int k) {
+      const BlockHost &bh = p->blocks[b];
+      return p->blocks[b].db.cell0 +
+             plane_row_base(bh.PO.data(), bh.F.data(), bh.d.nx + bh.d.ny - 2, bh.d.nx, i + j + k, k) + j;
+    };
+    auto add = [&](long long cell, long long nb, const void *src, long long pn) {
+      int &e = at_cell[(size_t)cell];
+      if (e < 0) {
+        e = (int)hents.size();
+        hents.push_back(HaloEntry{cell, {-1, -1}, {0.0, 0.0}});
+      }
+      const int slot = hents[e].nb[0] < 0 ? 0 : 1;
+      hents[e].nb[slot] = nb;
+      hsrcs.push_back(HaloSrc{e, slot, src, pn});
+    };
+    for (const sip_interface &f : p->ifaces) {
+      const sip_block_desc &L = blocks[f.blk_lo], &H = blocks[f.blk_hi];
+      for (int k = 0; k < f.nk; ++k)
+        for (int j = 0; j < f.nj; ++j) {
+          const long long cl = cell_of(f.blk_lo, L.nx - 1, j, k), ch = cell_of(f.blk_hi, 0, j, k);
+          const long long pl = (long long)(L.nx - 1) + (long long)L.nx * (j + (long long)L.ny * k);
+          const long long ph = (long long)H.nx * (j + (long long)H.ny * k);
+          add(cl, ch, L.ae, pl);
+          if (sym) add(ch, cl, L.ae, pl);  // symmetric: the entry of hi equals lo's AE
+          else add(ch, cl, H.aw, ph);
+        }
+    }
+    p->nhalo = (int)hents.size();
+    HaloSrc *dsrc = nullptr;
+    PA(p->beff64, N);
+    PA(p->halo, p->nhalo);
+    PA(dsrc, hsrcs.size());
+    cudaError_t e = cudaMemcpyAsync(p->halo, hents.data(), hents.size() * sizeof(HaloEntry),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dsrc, hsrcs.data(), hsrcs.size() * sizeof(HaloSrc), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_halo_coefs(dsrc, (int)hsrcs.size(), p->halo, p->a32in ? 1 : 0, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    pfree(p, dsrc, hsrcs.size() * sizeof(HaloSrc));
+    if (e != cudaSuccess) return bail(e, "interfaces");
+  }
   {
     std::vector<int> tab;
     tab.reserve(tab_total);

@@ -170,6 +170,26 @@ constexpr int kNoallocParts = 16384;
 constexpr int kNoallocMaxDevices = 64;
 cudaError_t noalloc_scratch(int device, double **out);
 
+// x-interface coupling of a multi-block plan (lagged block Jacobi): every
+// interface face cell `cell` of a block gets beff[cell] = b[cell] -
+// c[0] x[nb[0]] - c[1] x[nb[1]] from its neighbours' current x (nb[1] = -1:
+// one coupling only).  Plan-global cell indices.
+struct HaloEntry {
+  long long cell;
+  long long nb[2];
+  double c[2];
+};
+// where the coupling coefficient c[slot] of entry e comes from: element p of a
+// natural-layout coefficient array of the caller (double or float)
+struct HaloSrc {
+  int e, slot;
+  const void *src;
+  long long p;
+};
+cudaError_t launch_halo_coefs(const HaloSrc *src, int nsrc, HaloEntry *ent, int coef_f32, cudaStream_t st);
+cudaError_t launch_halo(const HaloEntry *ent, int nent, const double *b, const double *x, double *beff,
+                        const Ctl *ctl, cudaStream_t st);
+
 // finalize modes
 constexpr int FIN_BNORM = 0;   // partials are ||b||^2 pieces: set ctl->bnorm
 constexpr int FIN_RELRES = 1;  // partials are ||r||^2 pieces: relres, stop rule, counters

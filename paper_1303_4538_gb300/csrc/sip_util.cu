@@ -223,6 +223,38 @@ cudaError_t launch_finalize(const double *partials, int n, Ctl *ctl, double *his
 
 // Start a sequence: counters and flags reset, both epoch slots moved past
 // every tag used so far (so no stale face word can match).
+// ------------------------------------------------------------ interfaces
+__global__ void k_halo_coefs(const HaloSrc *src, int nsrc, HaloEntry *ent, int coef_f32) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nsrc; q += gridDim.x * blockDim.x) {
+    const HaloSrc s = src[q];
+    ent[s.e].c[s.slot] = coef_f32 ? (double)((const float *)s.src)[s.p] : ((const double *)s.src)[s.p];
+  }
+}
+
+cudaError_t launch_halo_coefs(const HaloSrc *src, int nsrc, HaloEntry *ent, int coef_f32, cudaStream_t st) {
+  k_halo_coefs<<<util_grid(nsrc), 256, 0, st>>>(src, nsrc, ent, coef_f32);
+  return cudaGetLastError();
+}
+
+// Lagged interface terms of the coupled residual, in interface order:
+// beff = b - c0 x_nb0 (- c1 x_nb1).  Skipped once the stop rule has fired.
+__global__ void k_halo(const HaloEntry *ent, int nent, const double *b, const double *x, double *beff,
+                       const Ctl *ctl) {
+  if (ctl->done) return;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nent; q += gridDim.x * blockDim.x) {
+    const HaloEntry e = ent[q];
+    double v = b[e.cell] - e.c[0] * x[e.nb[0]];
+    if (e.nb[1] >= 0) v -= e.c[1] * x[e.nb[1]];
+    beff[e.cell] = v;
+  }
+}
+
+cudaError_t launch_halo(const HaloEntry *ent, int nent, const double *b, const double *x, double *beff,
+                        const Ctl *ctl, cudaStream_t st) {
+  k_halo<<<util_grid(nent), 256, 0, st>>>(ent, nent, b, x, beff, ctl);
+  return cudaGetLastError();
+}
+
 __global__ void k_set_ctl(Ctl *ctl, double rtol, int max_iters) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     ctl->iter = 0;

@@ -15,7 +15,7 @@ class GpuSystem:
     """One or more blocks on the device with a factored plan."""
 
     def __init__(self, blocks, alpha=0.92, mode=sip.SIP_MODE_F64, inner=4, x0=None, tile=None,
-                 sym_null=False, coef_f32=False, max_spin=0, stall=0):
+                 sym_null=False, coef_f32=False, max_spin=0, stall=0, ifaces=None):
         torch = torch_cuda()
         if not isinstance(blocks, (list, tuple)):
             blocks = [blocks]
@@ -44,7 +44,14 @@ class GpuSystem:
         if tile:
             opts.tile_j, opts.tile_k = tile
         torch.cuda.synchronize()
-        self.plan = sip.Plan(self.ctx, descs, opts, keep=(self.A, self.b, self.x))
+        ifs = None
+        if ifaces:
+            ifs = []
+            for lo, hi, nj, nk in ifaces:
+                f = sip.sip_interface()
+                f.blk_lo, f.blk_hi, f.nj, f.nk = lo, hi, nj, nk
+                ifs.append(f)
+        self.plan = sip.Plan(self.ctx, descs, opts, ifaces=ifs, keep=(self.A, self.b, self.x))
 
     def xs(self, n=0):
         return self.x[n].cpu().numpy()
