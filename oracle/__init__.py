@@ -65,6 +65,8 @@ def lib():
         L.oracle_iterate_f32.restype = None
         L.oracle_solve_refined.argtypes = [I, I, I] + [P] * 23 + [D, I, I, P, P]
         L.oracle_solve_refined.restype = I
+        L.oracle_solve_f32.argtypes = [I, I, I] + [P] * 16 + [D, I, P, P]
+        L.oracle_solve_f32.restype = I
         L.oracle_solve_mb.argtypes = [I, P, P, P, P, P, I, P, I, D, I, P, P]
         L.oracle_solve_mb.restype = I
         _lib = L
@@ -200,6 +202,21 @@ def solve_refined(nx, ny, nz, coefs64, coefs32, factors32, b, x0=None, rtol=1e-8
     it = lib().oracle_solve_refined(nx, ny, nz, *[_p(a) for a in A64], *[_p(a) for a in A32],
                                     *[_p(f) for f in F], _p(b), _p(x), float(rtol), int(max_outer),
                                     int(m_inner), _p(hist), ctypes.byref(rel))
+    return x, it, rel.value, hist[: it + 1].copy()
+
+
+def solve_f32(nx, ny, nz, coefs32, factors32, b, x0=None, rtol=1e-8, max_iters=100):
+    """The paper's single-precision SIP (Sec. 4.1): float copies of A, of the
+    factors, of b and x; returns (x (FP64), n, relres, hist)."""
+    A32 = _coefs(coefs32, _f32)
+    F = [_f32(f) for f in factors32]
+    b = _f64(b)
+    n = nx * ny * nz
+    x = np.zeros(n) if x0 is None else _f64(x0).copy()
+    hist = np.zeros(max_iters + 1)
+    rel = ctypes.c_double(0.0)
+    it = lib().oracle_solve_f32(nx, ny, nz, *[_p(a) for a in A32], *[_p(f) for f in F], _p(b), _p(x),
+                                float(rtol), int(max_iters), _p(hist), ctypes.byref(rel))
     return x, it, rel.value, hist[: it + 1].copy()
 
 

@@ -51,7 +51,8 @@
  * L U = A + N, by alpha = 0 (ILU(0)) and by the 1-D case (exact LU); the
  * iteration by the dense preconditioned-Richardson step and by convergence to
  * the dense solution; the single-precision and refinement drivers by
- * convergence to the FP64 solution; the multi-block solve by the dense
+ * convergence to the FP64 solution; the single-precision solve by tracking the
+ * FP64 history until it stagnates at the float level; the multi-block solve by the dense
  * global residual, the dense block-Jacobi Richardson step and convergence to
  * the dense global solution on tiny meshes.  No value printed in the paper can be
  * matched (it prints none for SIP).
@@ -460,6 +461,52 @@ int oracle_solve_mb(int nb, const int *dims, const double *const *A, const doubl
   }
   for (int b = 0; b < nb; ++b) { free(beff[b]); free(r[b]); }
   free(beff); free(r); free(y); free(d);
+  if (relres_out) *relres_out = rel;
+  return it;
+}
+
+/* ------------------------------------------------------------------ */
+/* The paper's single-precision relaxation (Sec. 4.1): right-hand side and
+ * solution converted to float, every SIP step in float with float copies of
+ * A and of the factors, x converted back at the end.  relres(x_n) is computed
+ * from the float residual (its squares summed in double) over ||b||_2 of the
+ * double right-hand side; stop rule as oracle_solve.  Returns n; hist
+ * (nullable, max_iters + 1) gets relres(x_0..x_n). */
+int oracle_solve_f32(int nx, int ny, int nz,
+                     const float *ap, const float *aw, const float *ae, const float *as,
+                     const float *an, const float *ab, const float *at,
+                     const float *lb, const float *lw, const float *ls, const float *lp,
+                     const float *un, const float *ue, const float *ut,
+                     const double *b, double *x, double rtol, int max_iters,
+                     double *hist, double *relres_out) {
+  size_t n = (size_t)nx * ny * nz;
+  float *b32 = (float *)malloc(n * sizeof(float));
+  float *x32 = (float *)malloc(n * sizeof(float));
+  float *r = (float *)malloc(n * sizeof(float));
+  float *y = (float *)malloc(n * sizeof(float));
+  float *d = (float *)malloc(n * sizeof(float));
+  for (size_t p = 0; p < n; ++p) {
+    b32[p] = (float)b[p];
+    x32[p] = (float)x[p];
+  }
+  double bb = sqrt(oracle_dot_sq((int64_t)n, b));
+  double scale = bb > 0.0 ? bb : 1.0;
+  int it = 0;
+  double rel = 0.0;
+  for (;;) {
+    f32_residual(nx, ny, nz, ap, aw, ae, as, an, ab, at, b32, x32, r, 0);
+    nsum acc = {0.0, 0.0};
+    for (size_t p = 0; p < n; ++p) nsum_add(&acc, (double)r[p] * (double)r[p]);
+    rel = sqrt(nsum_get(&acc)) / scale;
+    if (hist) hist[it] = rel;
+    if (rel <= rtol || it >= max_iters) break;
+    f32_forward(nx, ny, nz, lb, lw, ls, lp, r, y);
+    f32_backward(nx, ny, nz, un, ue, ut, y, d);
+    for (size_t p = 0; p < n; ++p) x32[p] += d[p];
+    ++it;
+  }
+  for (size_t p = 0; p < n; ++p) x[p] = (double)x32[p];
+  free(b32); free(x32); free(r); free(y); free(d);
   if (relres_out) *relres_out = rel;
   return it;
 }

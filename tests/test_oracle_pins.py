@@ -238,6 +238,30 @@ def test_single_precision_iteration_tracks_fp64():
     assert np.array_equal(y1, y2)
 
 
+@pytest.mark.parametrize("kind", ["convdiff", "poisson"])
+def test_single_precision_solve_tracks_then_stagnates(kind):
+    """The paper's FP32 relaxation follows the FP64 relres history while it is
+    far above float resolution; on the fast-converging Poisson system it then
+    stagnates near the float level while FP64 keeps converging."""
+    nx, ny, nz = 9, 8, 7
+    blk = W.make_block(nx, ny, nz, seed=73, kind=kind)
+    F = oracle.factor(nx, ny, nz, blk.coefs, 0.92)
+    F32 = oracle.factors_f32(F)
+    c32 = {k: v.astype(np.float32) for k, v in blk.coefs.items()}
+    x64, it64, rel64, h64 = oracle.solve(nx, ny, nz, blk.coefs, F, blk.b, rtol=-1.0, max_iters=200)
+    x32, it32, rel32, h32 = oracle.solve_f32(nx, ny, nz, c32, F32, blk.b, rtol=-1.0, max_iters=200)
+    assert it32 == 200 and len(h32) == 201
+    big = h64 > 1e-4
+    assert np.all(np.abs(h32[big] - h64[big]) <= 1e-4 * h64[big] + 1e-6)
+    if kind == "poisson":
+        assert 1e-9 < h32[-1] < 1e-6            # stagnation at the float level
+        assert h64[-1] < 1e-12                   # while FP64 keeps converging
+        assert np.abs(x32 - blk.xstar).max() <= 1e-5
+    # stop rule: with a reachable tolerance the float solve stops like the FP64 one
+    _, itA, relA, _ = oracle.solve_f32(nx, ny, nz, c32, F32, blk.b, rtol=1e-3, max_iters=200)
+    assert relA <= 1e-3 and h32[itA] == relA and h32[itA - 1] > 1e-3
+
+
 @pytest.mark.parametrize("m", [1, 2, 4, 8])
 def test_refinement_reaches_fp64_solution(m):
     nx, ny, nz = 8, 7, 6
