@@ -63,7 +63,10 @@ typedef struct sip_plan sip_plan;
 typedef enum {
   SIP_MODE_F64 = 0,         /* FP64 sweeps, FP64 factors */
   SIP_MODE_F32_REFINED = 1, /* FP32 sweeps inside an FP64 residual / refinement loop */
-  SIP_MODE_F32 = 2          /* FP32 sweeps only (the paper's single-precision relaxation) */
+  SIP_MODE_F32 = 2          /* FP32 only (the paper's single-precision relaxation, Sec. 4.1): rhs
+                               and solution converted to single, residual, norm and sweeps in
+                               FP32, the result converted back; relres is that of the FP32
+                               residual and stagnates near the single-precision level */
 } sip_mode;
 
 /* One block's system.  Lifetimes: the coefficient arrays are read during
@@ -106,6 +109,9 @@ typedef struct {
   int32_t stages;          /* depth of the sweeps' shared-memory prefetch ring: 0 (auto), 4 or 6 */
   int32_t debug_stall;     /* test hook: 1 makes the sweeps wait for a tag no producer
                               writes, so the bounded waits time out (SIP_ERR_DEVICE_TIMEOUT) */
+  int32_t graphs;          /* 1: queue iterations by replaying CUDA graphs captured on the
+                              context's stream (one replay per 16 iterations; needs a
+                              non-NULL stream, ignored while profiling); 0: launch by launch */
 } sip_options;
 
 /* Fills *opt with defaults: alpha 0.92, SIP_MODE_F64, inner_iters 4. Host pointer. */

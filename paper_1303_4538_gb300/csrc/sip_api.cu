@@ -134,6 +134,10 @@ struct sip_plan {
   double *beff64 = nullptr;
   HaloEntry *halo = nullptr;
   int nhalo = 0;
+  // captured iterations (sip_options.graphs): graph[0] replays one iteration,
+  // graph[1] a chunk of kChunk iterations; kernels launched per replay
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  long long graph_kernels[2] = {0, 0};
 };
 
 // ------------------------------------------------------------------ helpers
@@ -161,6 +165,9 @@ void pfree(sip_plan *p, void *v, size_t bytes) {
 }
 
 void free_plan_memory(sip_plan *p) {
+  for (auto &g : p->graph)
+    if (g) cudaGraphExecDestroy(g);
+  p->graph[0] = p->graph[1] = nullptr;
   for (auto &r : p->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -266,6 +273,8 @@ int check_status(sip_plan *p) {
 // Interface terms of the coupled residual from the current x (lagged block Jacobi).
 int enqueue_halo(sip_plan *p) {
   sip_ctx *ctx = p->ctx;
+  if (p->nhalo > 0 && p->mode == SIP_MODE_F32)
+    UTIL(launch_cast_f32_f64(p->d32, p->x64, p->ncells, ctx->stream));  // the FP32 iterate is the current x
   if (p->nhalo > 0) UTIL(launch_halo(p->halo, p->nhalo, p->b64, p->x64, p->beff64, p->ctl, ctx->stream));
   return SIP_OK;
 }
@@ -337,8 +346,87 @@ int enqueue_iter_refined(sip_plan *p) {
   return SIP_OK;
 }
 
+// One single-precision SIP iteration (the paper's FP32 relaxation, Sec. 4.1):
+// residual, norm and forward substitution in FP32 on the converted rhs
+// (r32) and solution (d32), then the FP32 backward substitution and update.
+int enqueue_iter_f32(sip_plan *p) {
+  sip_ctx *ctx = p->ctx;
+  if (int rc = enqueue_halo(p)) return rc;
+  if (p->nhalo > 0) UTIL(launch_cast_f64_f32(p->beff64, p->r32, p->ncells, ctx->stream));
+  FwdParams<float> f;
+  const int fk = p->sym ? K_FWD32SN : K_FWD32N;
+  f.c = common(p, false, 0, 1, 0, fk);
+  f.rec = (const float *)p->recF;
+  f.rsf = p->rsf;
+  f.b = p->r32;
+  f.x = p->d32;
+  f.y = p->y32;
+  f.partials = p->partials;
+  CU(launch(p, fk, f));
+  UTIL(launch_finalize(p->partials, p->ntiles, p->ctl, p->hist, p->hist_cap, p->status, FIN_RELRES, ctx->stream));
+  BwdParams<float> b;
+  b.c = common(p, true, 1, 0, 1, K_BWD32);
+  b.rec = (const float *)p->recB;
+  b.y = p->y32;
+  b.x = p->d32;
+  b.x64 = nullptr;
+  CU(launch(p, K_BWD32, b));
+  return SIP_OK;
+}
+
 int enqueue_iter(sip_plan *p) {
-  return p->mode == SIP_MODE_F32_REFINED ? enqueue_iter_refined(p) : enqueue_iter_f64(p);
+  if (p->mode == SIP_MODE_F32_REFINED) return enqueue_iter_refined(p);
+  if (p->mode == SIP_MODE_F32) return enqueue_iter_f32(p);
+  return enqueue_iter_f64(p);
+}
+
+constexpr int kChunk = 16;  // iterations queued per host check of the control block
+
+// Capture `iters` iterations of the plan into an executable graph.  Every
+// launch of an iteration has plan-constant arguments (epochs, tickets and the
+// stop flag live in device memory), so one capture replays any iteration.
+int capture_iters(sip_plan *p, int slot, int iters) {
+  sip_ctx *ctx = p->ctx;
+  const long long l0 = p->launches;
+  cudaGraph_t g = nullptr;
+  CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = SIP_OK;
+  for (int it = 0; it < iters && rc == SIP_OK; ++it) rc = enqueue_iter(p);
+  const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+  if (rc != SIP_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(ctx, SIP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  const cudaError_t e2 = cudaGraphInstantiate(&p->graph[slot], g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) {
+    p->graph[slot] = nullptr;
+    return fail(ctx, SIP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
+  }
+  p->graph_kernels[slot] = p->launches - l0;
+  p->launches = l0;
+  return SIP_OK;
+}
+
+// Queue n iterations: from the captured graphs when the plan uses them (and
+// no per-launch profiling is on), else launch by launch.
+int enqueue_iters(sip_plan *p, int n) {
+  sip_ctx *ctx = p->ctx;
+  if (!p->opt.graphs || p->prof || ctx->stream == nullptr) {
+    for (int it = 0; it < n; ++it)
+      if (int rc = enqueue_iter(p)) return rc;
+    return SIP_OK;
+  }
+  while (n > 0) {
+    const int slot = n >= kChunk ? 1 : 0;
+    if (!p->graph[slot])
+      if (int rc = capture_iters(p, slot, slot ? kChunk : 1)) return rc;
+    CU(cudaGraphLaunch(p->graph[slot], ctx->stream));
+    p->launches += p->graph_kernels[slot];
+    n -= slot ? kChunk : 1;
+  }
+  return SIP_OK;
 }
 
 // Copy b and x of every block into the plan layout, ||b||, control reset.
@@ -354,12 +442,17 @@ int begin_sequence(sip_plan *p, double rtol, int max_iters) {
     CU(cudaMemcpyAsync(p->beff64, p->b64, (size_t)p->ncells * sizeof(double), cudaMemcpyDeviceToDevice,
                        ctx->stream));
   UTIL(launch_sumsq_partials(p->b64, p->ncells, p->bparts, p->nbparts, ctx->stream));
+  if (p->mode == SIP_MODE_F32) {  // rhs and solution converted to single precision
+    UTIL(launch_cast_f64_f32(p->b64, p->r32, p->ncells, ctx->stream));
+    UTIL(launch_cast_f64_f32(p->x64, p->d32, p->ncells, ctx->stream));
+  }
   UTIL(launch_finalize(p->bparts, p->nbparts, p->ctl, p->hist, p->hist_cap, p->status, FIN_BNORM, ctx->stream));
   return SIP_OK;
 }
 
 int end_sequence(sip_plan *p) {
   sip_ctx *ctx = p->ctx;
+  if (p->mode == SIP_MODE_F32) UTIL(launch_cast_f32_f64(p->d32, p->x64, p->ncells, ctx->stream));
   for (auto &bh : p->blocks) UTIL(launch_from_plan_f64(p->x64, bh.d.x, bh.db, ctx->stream));
   CU(cudaMemcpyAsync(&p->h_ctl[2], p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
   int rc = check_status(p);  // synchronises
@@ -371,6 +464,7 @@ int end_sequence(sip_plan *p) {
 // kernels a plan of the given mode launches
 std::vector<int> plan_kinds(int mode, bool sym, bool a32in) {
   if (mode == SIP_MODE_F64) return {K_FACTOR, sym ? K_FWD64S : K_FWD64, K_BWD64};
+  if (mode == SIP_MODE_F32) return {K_FACTOR32, sym ? K_FWD32SN : K_FWD32N, K_BWD32};
   std::vector<int> k = {K_FACTOR32, K_FWD32Z, sym ? K_FWD32S : K_FWD32, K_BWD32, K_BWD32Z, K_BWD32U, K_BWD32ZU};
   k.push_back(a32in ? (sym ? K_RES32AS : K_RES32A) : (sym ? K_RES64S : K_RES64));
   return k;
@@ -505,7 +599,7 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
   if (opt_in) opt = *opt_in;
   else sip_default_options(&opt);
   if (!(opt.alpha >= 0.0 && opt.alpha <= 1.0)) return fail(ctx, SIP_ERR_INVALID_ARG, "alpha must lie in [0, 1]");
-  if (opt.mode != SIP_MODE_F64 && opt.mode != SIP_MODE_F32_REFINED)
+  if (opt.mode != SIP_MODE_F64 && opt.mode != SIP_MODE_F32_REFINED && opt.mode != SIP_MODE_F32)
     return fail(ctx, SIP_ERR_INVALID_ARG, "unsupported mode");
   if (opt.mode == SIP_MODE_F32_REFINED && opt.inner_iters < 1)
     return fail(ctx, SIP_ERR_INVALID_ARG, "inner_iters must be >= 1");
@@ -673,7 +767,7 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     PA(p->r32, N);
     PA(p->d32, N);
     PA(p->y32, N);
-    if (!p->a32in) PA(p->arec64, N * (sym ? 4 : 8));
+    if (!p->a32in && p->mode == SIP_MODE_F32_REFINED) PA(p->arec64, N * (sym ? 4 : 8));
   }
   {
     cudaError_t e = cudaMallocHost(&p->h_ctl, 3 * sizeof(Ctl));
@@ -834,10 +928,8 @@ int sip_iterate(sip_plan *p, int niters, double *relres_out) {
   if (niters < 0) return fail(ctx, SIP_ERR_INVALID_ARG, "niters must be >= 0");
   int rc = begin_sequence(p, -1.0, niters);
   if (rc) return rc;
-  for (int it = 0; it < niters; ++it) {
-    rc = enqueue_iter(p);
-    if (rc) return rc;
-  }
+  rc = enqueue_iters(p, niters);
+  if (rc) return rc;
   rc = end_sequence(p);
   if (rc) return rc;
   if (relres_out) *relres_out = p->h_ctl[2].relres;
@@ -853,7 +945,7 @@ int sip_solve(sip_plan *p, double rtol, int max_iters, int *iters_out, double *r
   // Chunks of iterations; the stop rule runs on the device (kernels after the
   // deciding residual do nothing).  The host reads the control block once per
   // chunk, one chunk behind, so the next chunk is always queued.
-  const int chunk = 16;
+  const int chunk = kChunk;
   cudaEvent_t ev[2];
   CU(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
   CU(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
@@ -863,10 +955,8 @@ int sip_solve(sip_plan *p, double rtol, int max_iters, int *iters_out, double *r
   for (;;) {
     if (more) {
       const int n = std::min(chunk, max_iters + 1 - issued);
-      for (int it = 0; it < n; ++it) {
-        rc = enqueue_iter(p);
-        if (rc) return rc;
-      }
+      rc = enqueue_iters(p, n);
+      if (rc) return rc;
       issued += n;
       const int sl = nq & 1;
       CU(cudaMemcpyAsync(&p->h_ctl[sl], p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));

@@ -146,6 +146,8 @@ cudaError_t launch_sumsq_partials(const double *v, long long n, double *partials
 cudaError_t launch_finalize(const double *partials, int n, Ctl *ctl, double *hist, int hist_cap,
                             const int *status, int mode, cudaStream_t st);
 cudaError_t launch_set_ctl(Ctl *ctl, double rtol, int max_iters, cudaStream_t st);
+cudaError_t launch_cast_f64_f32(const double *src, float *dst, long long n, cudaStream_t st);
+cudaError_t launch_cast_f32_f64(const float *src, double *dst, long long n, cudaStream_t st);
 cudaError_t launch_export_factors(const void *recF, const void *recB, int is_f32, int rsf,
                                   double *const out[7], const DevBlock &hb, cudaStream_t st);
 

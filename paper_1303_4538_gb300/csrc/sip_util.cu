@@ -255,6 +255,23 @@ cudaError_t launch_halo(const HaloEntry *ent, int nent, const double *b, const d
   return cudaGetLastError();
 }
 
+__global__ void k_cast_f64_f32(const double *src, float *dst, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    dst[q] = (float)src[q];
+}
+__global__ void k_cast_f32_f64(const float *src, double *dst, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    dst[q] = (double)src[q];
+}
+cudaError_t launch_cast_f64_f32(const double *src, float *dst, long long n, cudaStream_t st) {
+  k_cast_f64_f32<<<util_grid(n), 256, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_cast_f32_f64(const float *src, double *dst, long long n, cudaStream_t st) {
+  k_cast_f32_f64<<<util_grid(n), 256, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
 __global__ void k_set_ctl(Ctl *ctl, double rtol, int max_iters) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     ctl->iter = 0;

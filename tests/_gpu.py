@@ -15,7 +15,7 @@ class GpuSystem:
     """One or more blocks on the device with a factored plan."""
 
     def __init__(self, blocks, alpha=0.92, mode=sip.SIP_MODE_F64, inner=4, x0=None, tile=None,
-                 sym_null=False, coef_f32=False, max_spin=0, stall=0, ifaces=None):
+                 sym_null=False, coef_f32=False, max_spin=0, stall=0, ifaces=None, graphs=0):
         torch = torch_cuda()
         if not isinstance(blocks, (list, tuple)):
             blocks = [blocks]
@@ -40,7 +40,7 @@ class GpuSystem:
             self.b.append(b)
             self.x.append(x)
         opts = sip.default_options(alpha=alpha, mode=mode, inner_iters=inner, max_spin=max_spin,
-                                   debug_stall=stall)
+                                   debug_stall=stall, graphs=graphs)
         if tile:
             opts.tile_j, opts.tile_k = tile
         torch.cuda.synchronize()
