@@ -198,6 +198,34 @@ int sip_residual_norm(sip_ctx *ctx, const sip_block_desc *blk, double *rnorm_out
 #define SIP_NOALLOC_MAX_CELLS 67108864LL
 int sip_residual_norm_noalloc(sip_ctx *ctx, const sip_block_desc *blk, double *norms_dev);
 
+/* ---- Serving (continuous batching of solve requests) ------------------
+ * A server runs `max_slots` solver slots, each with its own CUDA stream on the
+ * calling thread's current device.  Submitted requests queue in arrival order;
+ * a free slot admits the oldest request once its estimated device footprint
+ * fits in what is left of `hbm_budget_bytes` (a request larger than the whole
+ * budget runs alone), factors it (coefficient copies and factors stay on the
+ * device), solves it with sip_solve's stop rule and frees its memory.  Slots
+ * run concurrently, so requests arriving while others are on the GPU start as
+ * soon as a slot and memory free up, and their kernels overlap.
+ * The descriptor's arrays must stay valid (b and the coefficients unmodified)
+ * until the request is done; the solution is written into blk->x. */
+typedef struct sip_server sip_server;
+/* Starts the slots.  ctx: a context on the device to use (its stream is not
+ * used).  Errors: SIP_ERR_INVALID_ARG, SIP_ERR_NO_DEVICE. */
+int sip_server_start(sip_ctx *ctx, size_t hbm_budget_bytes, int max_slots, sip_server **srv);
+/* Queues one block (opt nullable: defaults); non-blocking.  *ticket (host)
+ * identifies the request.  Errors: SIP_ERR_INVALID_ARG, SIP_ERR_BUSY (4096
+ * requests waiting). */
+int sip_server_submit(sip_server *srv, const sip_block_desc *blk, const sip_options *opt, double rtol,
+                      int max_iters, uint64_t *ticket);
+/* Non-blocking state of a request (host outputs, nullable): done (0/1); once
+ * done, status (the sip_solve / sip_factor return code), iters and relres.  A
+ * finished ticket is reported once and then forgotten (SIP_ERR_NOT_FOUND). */
+int sip_server_poll(sip_server *srv, uint64_t ticket, int *done, int *status, int *iters, double *relres);
+/* Stops accepting requests, runs the queued ones to completion, joins the
+ * slots and frees the server. */
+int sip_server_stop(sip_server *srv);
+
 /* Measurement aids.  sip_profile_enable(plan, 1) records a CUDA event pair
  * on the plan's stream around every later kernel launch of the plan;
  * sip_profile_read synchronises the stream and writes, for each kernel kind

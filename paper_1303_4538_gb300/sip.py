@@ -43,7 +43,7 @@ EXPORTED = (
     "sip_iterate", "sip_solve", "sip_get_history", "sip_export_factors", "sip_plan_bytes",
     "sip_plan_destroy", "sip_plane_layout", "sip_profile_enable", "sip_profile_read",
     "sip_launch_count", "sip_kernel_name", "sip_residual_norm",
-    "sip_residual_norm_noalloc",
+    "sip_residual_norm_noalloc", "sip_server_start", "sip_server_submit", "sip_server_poll", "sip_server_stop",
 )
 
 
@@ -112,6 +112,12 @@ def lib():
         L.sip_kernel_name.argtypes = [I]
         L.sip_residual_norm.argtypes = [P, ctypes.POINTER(sip_block_desc), ctypes.POINTER(D), ctypes.POINTER(D)]
         L.sip_residual_norm_noalloc.argtypes = [P, ctypes.POINTER(sip_block_desc), P]
+        L.sip_server_start.argtypes = [P, ctypes.c_size_t, I, ctypes.POINTER(P)]
+        L.sip_server_submit.argtypes = [P, ctypes.POINTER(sip_block_desc), ctypes.POINTER(sip_options), D, I,
+                                        ctypes.POINTER(ctypes.c_uint64)]
+        L.sip_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                                      ctypes.POINTER(D)]
+        L.sip_server_stop.argtypes = [P]
         L.sip_kernel_name.restype = ctypes.c_char_p
         for name in EXPORTED:
             if name not in ("sip_default_options", "sip_last_error", "sip_kernel_name"):
@@ -269,6 +275,53 @@ def plane_layout(nx: int, ny: int, nz: int):
     if rc != SIP_OK:
         raise SipError(rc, "sip_plane_layout failed")
     return out
+
+
+class Server:
+    """sip_server_start / submit / poll / stop (continuous batching)."""
+
+    def __init__(self, ctx: "Context", hbm_budget_bytes: int, max_slots: int):
+        self.ctx = ctx
+        self.h = ctypes.c_void_p()
+        rc = lib().sip_server_start(ctx.h, ctypes.c_size_t(int(hbm_budget_bytes)), int(max_slots),
+                                    ctypes.byref(self.h))
+        if rc != SIP_OK:
+            raise SipError(rc, "sip_server_start failed")
+        self._keep = {}
+
+    def submit(self, desc: sip_block_desc, opts: Optional[sip_options], rtol: float, max_iters: int,
+               keep=None) -> int:
+        t = ctypes.c_uint64(0)
+        rc = lib().sip_server_submit(self.h, ctypes.byref(desc), ctypes.byref(opts) if opts is not None else None,
+                                     float(rtol), int(max_iters), ctypes.byref(t))
+        if rc != SIP_OK:
+            raise SipError(rc, "sip_server_submit failed")
+        self._keep[t.value] = keep  # tensors that must outlive the request
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while running, else (status, iters, relres)."""
+        d, st, it = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        rc = lib().sip_server_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(d), ctypes.byref(st),
+                                   ctypes.byref(it), ctypes.byref(rel))
+        if rc != SIP_OK:
+            raise SipError(rc, "sip_server_poll failed")
+        if not d.value:
+            return None
+        self._keep.pop(ticket, None)
+        return st.value, it.value, rel.value
+
+    def stop(self):
+        if self.h:
+            lib().sip_server_stop(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
 
 
 def kernel_names() -> List[str]:
