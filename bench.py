@@ -11,7 +11,9 @@ and x is copied back; x is reset to 0 before every step.  `value` is the
 FP32-refined solver's SIP rate in MLUP/s (cells x FP32 SIP iterations / step
 time, the FP64 residual/refinement passes included in the time); the plain
 FP64 solver is measured the same way under "fp64".  The factorisation is
-timed separately (factor_ms).
+timed separately (factor_ms).  "time_to_1e-8" times full solves of both
+solvers to the 1e-8 relative residual; "serving" measures the request server
+(continuous batching, p50/p99 latency) against a serial plain-FP64 queue.
 
 --impl reference times the CPU oracle (plain C, one thread) on a bounded
 sample of the same workload: each step is one FP64 SIP iteration of the
@@ -68,9 +70,12 @@ def parse():
     ap.add_argument("--iters", type=int, default=100,
                     help="max FP64 corrections (refined) / iterations (fp64) per step")
     ap.add_argument("--inner", type=int, default=4, help="FP32 iterations per FP64 correction")
-    ap.add_argument("--ttol", action="store_true", help="also time full solves to 1e-8")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=3)
+    ap.add_argument("--no-ttol", action="store_true", help="skip the time-to-1e-8 solves")
+    ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving measurement (0: skip)")
+    ap.add_argument("--serve-max-n", type=int, default=48, help="largest cube edge of a served request")
+    ap.add_argument("--serve-slots", type=int, default=4)
     return ap.parse_args()
 
 
@@ -328,7 +333,7 @@ def run_gb300(args):
     ms_e2e = e0.elapsed_time(e1)
 
     ttol = {}
-    if args.ttol:
+    if not args.no_ttol:
         for name, plan, inner in (("f32_refined", plan_r, args.inner), ("f64", plan_d, 1)):
             barrier()
             x.zero_()
@@ -403,12 +408,104 @@ def run_gb300(args):
     }
     if ttol:
         line["time_to_1e-8"] = ttol
+    if args.serve_requests > 0 and world == 1:
+        line["serving"] = serving(args, local)
     print(json.dumps(line), flush=True)
     plan_r.close()
     plan_d.close()
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def serving(args, local):
+    """Continuous batching of solve requests: Poisson arrivals at 0.8 x the
+    measured serial plain-FP64 capacity; the server (FP32-refined mode, CUDA
+    graphs, `serve_slots` concurrent slots) against a serial plain-FP64 queue
+    replayed with the measured service times.  Latency = arrival -> the host
+    sees the request done."""
+    import numpy as np
+    import torch
+
+    from paper_1303_4538_gb300 import sip
+    from paper_1303_4538_gb300 import workloads as W
+
+    rng = np.random.Generator(np.random.PCG64(4543))
+    N = args.serve_requests
+    reqs = []
+    for q in range(N):
+        n = int(rng.integers(16, args.serve_max_n + 1))
+        kind = "poisson" if rng.random() < 0.5 else "convdiff"
+        rtol = 1e-6 if rng.random() < 0.5 else 1e-8
+        blk = W.make_block(n, n, n, seed=4543 * 1000 + q, kind=kind)
+        A = [torch.from_numpy(c).cuda() for c in blk.coef_list()]
+        b = torch.from_numpy(blk.b).cuda()
+        x = torch.zeros(blk.n, dtype=torch.float64, device="cuda")
+        coefs = list(A)
+        if blk.symmetric:
+            coefs[1] = coefs[3] = coefs[5] = None
+        desc = sip.make_desc(blk.nx, blk.ny, blk.nz, coefs, b, x, symmetric=blk.symmetric)
+        reqs.append(dict(n=n, kind=kind, rtol=rtol, desc=desc, x=x, keep=(A, b, x)))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ctx = sip.Context(local, stream.cuda_stream)
+    o64 = sip.default_options(mode=sip.SIP_MODE_F64)
+    # serial plain FP64: service time of every request (plan + solve + result back)
+    for r in reqs[:2]:
+        r["x"].zero_()
+        p = sip.Plan(ctx, [r["desc"]], o64)
+        p.solve(r["rtol"], 5000)
+        p.close()
+    serv = []
+    for r in reqs:
+        r["x"].zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p = sip.Plan(ctx, [r["desc"]], o64)
+        p.solve(r["rtol"], 5000)
+        p.close()
+        serv.append(time.perf_counter() - t0)
+    cap = N / sum(serv)
+    lam = 0.8 * cap
+    arr = np.cumsum(rng.exponential(1.0 / lam, size=N))
+    # serial FIFO with the same arrivals
+    end, lat_ser = 0.0, []
+    for a, s_ in zip(arr, serv):
+        end = max(a, end) + s_
+        lat_ser.append(end - a)
+    # served run
+    for r in reqs:
+        r["x"].zero_()
+    torch.cuda.synchronize()
+    oref = sip.default_options(mode=sip.SIP_MODE_F32_REFINED, graphs=1)
+    srv = sip.Server(ctx, 64 << 30, args.serve_slots)
+    lat, fin, bad = [0.0] * N, [0.0] * N, 0
+    pending = {}
+    t0 = time.perf_counter()
+    i = 0
+    while i < N or pending:
+        now = time.perf_counter() - t0
+        while i < N and arr[i] <= now:
+            pending[srv.submit(reqs[i]["desc"], oref, reqs[i]["rtol"], 5000, keep=reqs[i]["keep"])] = i
+            i += 1
+        for t in list(pending):
+            res = srv.poll(t)
+            if res is not None:
+                k = pending.pop(t)
+                fin[k] = time.perf_counter() - t0
+                lat[k] = fin[k] - arr[k]
+                bad += res[0] != sip.SIP_OK
+        time.sleep(0.0002)
+    srv.stop()
+    ctx.close()
+    ms = lambda v, q: round(float(np.percentile(np.array(v) * 1e3, q)), 3)
+    return {"requests": N, "sizes": f"cubes 16..{args.serve_max_n}", "mix": "Poisson/conv-diff 50/50, rtol 1e-6/1e-8",
+            "arrivals_per_s": round(lam, 2), "served": {"mode": "f32_refined, CUDA graphs",
+                                                        "slots": args.serve_slots,
+                                                        "solves_per_s": round(N / (max(fin) - arr[0]), 2),
+                                                        "p50_ms": ms(lat, 50), "p99_ms": ms(lat, 99),
+                                                        "failed": int(bad)},
+            "serial_fp64": {"solves_per_s": round(cap, 2), "p50_ms": ms(lat_ser, 50), "p99_ms": ms(lat_ser, 99)}}
 
 
 def main():
