@@ -230,6 +230,17 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU path
+def reduce_over_ranks(dist, times_ms, counts, device):
+    """Replicas: the job's time is the slowest rank's (MAX), its work the sum
+    of all ranks' (SUM).  Returns (times, counts) as Python lists."""
+    import torch
+    t = torch.tensor([float(v) for v in times_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(v) for v in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return t.tolist(), c.tolist()
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -351,14 +362,11 @@ def run_gb300(args):
     val_d = rates(ms_d, lup_iters_d)
     val_e2e = rates(ms_e2e, e2e_iters)
     if dist:
-        t = torch.tensor([ms_r, ms_d, ms_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        c = torch.tensor([lup_iters_r, lup_iters_d, e2e_iters], dtype=torch.float64, device="cuda")
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        ms_r, ms_d, ms_e2e = t.tolist()
-        val_r = N * c[0].item() / (ms_r / 1e3) / 1e6
-        val_d = N * c[1].item() / (ms_d / 1e3) / 1e6
-        val_e2e = N * c[2].item() / (ms_e2e / 1e3) / 1e6
+        (ms_r, ms_d, ms_e2e), c = reduce_over_ranks(dist, [ms_r, ms_d, ms_e2e],
+                                                    [lup_iters_r, lup_iters_d, e2e_iters], "cuda")
+        val_r = N * c[0] / (ms_r / 1e3) / 1e6
+        val_d = N * c[1] / (ms_d / 1e3) / 1e6
+        val_e2e = N * c[2] / (ms_e2e / 1e3) / 1e6
 
     hbm, src = peaks()
 
