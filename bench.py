@@ -40,23 +40,20 @@ METRIC = "SIP MLUP/s & %HBM roofline, FP32-refined vs FP64; p50/p99 solve latenc
 
 # Algorithmic bytes per cell per launch of each kernel kind (each array read or
 # written once; neighbour values reused on chip).  Words of 8 B (FP64) or 4 B.
+# The residual kernels' figures are for a symmetric A (four stored entries).
 ALGO_BYTES = {
     "factor": 7 * 8 + 7 * 8,           # A in, LB LW LS 1/LP UN UE UT out
     "factor32": 7 * 8 + 7 * 4,         # A in (FP64), FP32 factors out
-    "fwd64": 14 * 8,                   # A(7) b x LB LW LS 1/LP in, y out
-    "fwd64_sym": 11 * 8,               # AP AE AN AT b x LB LW LS 1/LP in, y out
+    "resid64": 4 * 8 + 3 * 8,          # AP AE AN AT b x in, r out
+    "resid32": 4 * 4 + 3 * 4, "resid32_norm": 4 * 4 + 3 * 4,
+    "resid64_r32": 4 * 8 + 2 * 8 + 4,  # AP AE AN AT b x in (FP64), r out (FP32)
+    "fwd64": 6 * 8,                    # LB LW LS 1/LP r in, y out
     "bwd64": 6 * 8,                    # UE UN UT y x in, x out
-    "fwd32": 14 * 4, "fwd32_norm": 14 * 4,
-    "fwd32_sym": 11 * 4, "fwd32_sym_norm": 11 * 4,
-    "fwd32_x0": 6 * 4,                 # LB LW LS 1/LP r in, y out
+    "fwd32": 6 * 4,
     "bwd32": 6 * 4,                    # UE UN UT y d in, d out
     "bwd32_x0": 5 * 4,                 # UE UN UT y in, d out
     "bwd32_upd64": 5 * 4 + 16,         # UE UN UT y d in, x64 in/out
     "bwd32_x0_upd64": 4 * 4 + 16,      # UE UN UT y in, x64 in/out
-    "resid64": 7 * 8 + 16 + 4,         # A(7) b x in, r32 out
-    "resid64_sym": 4 * 8 + 16 + 4,
-    "resid64_a32": 7 * 4 + 16 + 4,
-    "resid64_a32_sym": 4 * 4 + 16 + 4,
 }
 
 
@@ -138,7 +135,7 @@ class ClockSampler:
         return out
 
 
-SWEEP_SOURCES = ("sip_sweeps.cuh", "sip_layout.h", "sip_k32.cu", "sip_k64.cu", "sip_kres.cu")
+SWEEP_SOURCES = ("sip_sweeps.cuh", "sip_layout.h", "sip_k32.cu", "sip_k64.cu", "sip_resrow.cu")
 
 
 def src_hash() -> str:

@@ -98,13 +98,15 @@ struct sip_plan {
   DevBlock *d_blocks = nullptr;
   Tile *d_tiles_f = nullptr, *d_tiles_b = nullptr;
   int *d_tab = nullptr;
-  void *recF = nullptr, *recB = nullptr;  // FP64 (F64 mode) or FP32 (refined) records
-  int rsf = 8;                            // values per forward record
-  double *arec64 = nullptr;               // refined mode: FP64 A for the outer residual
+  void *recF = nullptr, *recB = nullptr;  // L and U records, FP64 (F64 mode) or FP32
+  void *recA = nullptr;                   // A records in the sweep precision
+  double *arec64 = nullptr;               // refined mode, FP64 coefficients: FP64 A of the outer residual
+  long long nrows = 0;                    // plane rows of all blocks (row-parallel kernels)
+  int rowgrid = 1;                        // CTAs of a row-parallel launch (plan constant: fixes the norm's sum order)
   double *b64 = nullptr, *x64 = nullptr, *y64 = nullptr;
   float *r32 = nullptr, *d32 = nullptr, *y32 = nullptr;
   uint64_t *faces = nullptr;
-  double *partials = nullptr;
+  double *partials = nullptr;  // [rowgrid] per-CTA sums of r^2
   double *bparts = nullptr;
   int nbparts = 1024;
   Ctl *ctl = nullptr;
@@ -279,69 +281,93 @@ int enqueue_halo(sip_plan *p) {
   return SIP_OK;
 }
 
-int enqueue_iter_f64(sip_plan *p) {
+// Residual r = b - A x over the whole plan (row-parallel kernel), with the
+// per-CTA r^2 partials when `norm`.
+template <typename TA, typename TX, typename TR>
+int enqueue_resid(sip_plan *p, int kind, const TA *arec, const TX *b, const TX *x, TR *r, bool norm) {
   sip_ctx *ctx = p->ctx;
-  if (int rc = enqueue_halo(p)) return rc;
-  FwdParams<double> f;
-  f.c = common(p, false, 0, 1, 0, p->sym ? K_FWD64S : K_FWD64);
-  f.rec = (const double *)p->recF;
-  f.rsf = p->rsf;
-  f.b = p->beff64 ? p->beff64 : p->b64;
-  f.x = p->x64;
-  f.y = p->y64;
-  f.partials = p->partials;
-  CU(launch(p, p->sym ? K_FWD64S : K_FWD64, f));
-  UTIL(launch_finalize(p->partials, p->ntiles, p->ctl, p->hist, p->hist_cap, p->status, FIN_RELRES, ctx->stream));
-  BwdParams<double> b;
-  b.c = common(p, true, 1, 0, 1, K_BWD64);
-  b.rec = (const double *)p->recB;
-  b.y = p->y64;
-  b.x = p->x64;
-  b.x64 = nullptr;
-  CU(launch(p, K_BWD64, b));
+  RowParams<TA, TX, TR> prm;
+  prm.blocks = p->d_blocks;
+  prm.nblocks = (int)p->blocks.size();
+  prm.nrows = p->nrows;
+  prm.ctl = p->ctl;
+  prm.status = p->status;
+  prm.arec = arec;
+  prm.b = b;
+  prm.x = x;
+  prm.r = r;
+  prm.partials = norm ? p->partials : nullptr;
+  ProfScope ps(p, kind);
+  CU(launch_resrow(prm, p->sym, p->rowgrid, ctx->stream));
   return SIP_OK;
+}
+
+// Forward substitution y = L^-1 r (in place when r == y).
+template <typename T>
+int enqueue_forward(sip_plan *p, int kind, const T *r, T *y) {
+  sip_ctx *ctx = p->ctx;
+  FwdParams<T> f;
+  f.c = common(p, false, 0, 1, 0, kind);
+  f.rec = (const T *)p->recF;
+  f.r = r;
+  f.y = y;
+  CU(launch(p, kind, f));
+  return SIP_OK;
+}
+
+// Backward substitution d = U^-1 y and the update (x <- x + d, or x64 += d).
+template <typename T>
+int enqueue_backward(sip_plan *p, int kind, const T *y, T *x, double *x64) {
+  sip_ctx *ctx = p->ctx;
+  BwdParams<T> b;
+  b.c = common(p, true, 1, 0, 1, kind);
+  b.rec = (const T *)p->recB;
+  b.y = y;
+  b.x = x;
+  b.x64 = x64;
+  CU(launch(p, kind, b));
+  return SIP_OK;
+}
+
+int enqueue_relres(sip_plan *p) {
+  sip_ctx *ctx = p->ctx;
+  UTIL(launch_finalize(p->partials, p->rowgrid, p->ctl, p->hist, p->hist_cap, p->status, FIN_RELRES, ctx->stream));
+  return SIP_OK;
+}
+
+// One FP64 SIP iteration (Sec. 1): r = b - A x and its norm (stop rule),
+// y = L^-1 r in place, then x <- x + U^-1 y.
+int enqueue_iter_f64(sip_plan *p) {
+  if (int rc = enqueue_halo(p)) return rc;
+  const double *b = p->beff64 ? p->beff64 : p->b64;
+  if (int rc = enqueue_resid(p, K_RES64, (const double *)p->recA, b, p->x64, p->y64, true)) return rc;
+  if (int rc = enqueue_relres(p)) return rc;
+  if (int rc = enqueue_forward(p, K_FWD64, p->y64, p->y64)) return rc;
+  return enqueue_backward(p, K_BWD64, p->y64, p->x64, (double *)nullptr);
 }
 
 // One FP64 correction of the refinement: FP64 residual (+ stop rule), then
 // m FP32 SIP iterations on A d = r from d = 0, the last adding d to x.
 int enqueue_iter_refined(sip_plan *p) {
-  sip_ctx *ctx = p->ctx;
   const int m = std::max(1, p->opt.inner_iters);
   if (int rc = enqueue_halo(p)) return rc;
   const double *bres = p->beff64 ? p->beff64 : p->b64;
-  if (p->a32in) {
-    ResParams<float> r;
-    r.blocks = p->d_blocks; r.tiles = p->d_tiles_f; r.ntiles = p->ntiles; r.tab_ints = p->tab_ints;
-    r.ctl = p->ctl; r.status = p->status;
-    r.arec = (const float *)p->recF + 4;
-    r.astride = p->rsf;
-    r.b = bres; r.x = p->x64; r.r32 = p->r32; r.partials = p->partials;
-    CU(launch(p, p->sym ? K_RES32AS : K_RES32A, r));
-  } else {
-    ResParams<double> r;
-    r.blocks = p->d_blocks; r.tiles = p->d_tiles_f; r.ntiles = p->ntiles; r.tab_ints = p->tab_ints;
-    r.ctl = p->ctl; r.status = p->status;
-    r.arec = p->arec64;
-    r.astride = p->sym ? 4 : 8;
-    r.b = bres; r.x = p->x64; r.r32 = p->r32; r.partials = p->partials;
-    CU(launch(p, p->sym ? K_RES64S : K_RES64, r));
-  }
-  UTIL(launch_finalize(p->partials, p->ntiles, p->ctl, p->hist, p->hist_cap, p->status, FIN_RELRES, ctx->stream));
+  int rc = p->arec64 ? enqueue_resid(p, K_RES64R, (const double *)p->arec64, bres, p->x64, p->r32, true)
+                     : enqueue_resid(p, K_RES64R, (const float *)p->recA, bres, p->x64, p->r32, true);
+  if (rc) return rc;
+  if ((rc = enqueue_relres(p))) return rc;
   for (int q = 0; q < m; ++q) {
     const bool first = q == 0, lastq = q == m - 1;
-    FwdParams<float> f;
-    const int fk = first ? K_FWD32Z : (p->sym ? K_FWD32S : K_FWD32);
-    f.c = common(p, false, 0, 1, 0, fk);
-    f.rec = (const float *)p->recF;
-    f.rsf = p->rsf;
-    f.b = p->r32; f.x = p->d32; f.y = p->y32; f.partials = nullptr;
-    CU(launch(p, fk, f));
-    BwdParams<float> b;
+    if (first) {
+      rc = enqueue_forward(p, K_FWD32, (const float *)p->r32, p->y32);  // d = 0: the residual is r
+    } else {
+      rc = enqueue_resid(p, K_RES32, (const float *)p->recA, (const float *)p->r32, (const float *)p->d32, p->y32,
+                         false);
+      if (!rc) rc = enqueue_forward(p, K_FWD32, (const float *)p->y32, p->y32);
+    }
+    if (rc) return rc;
     const int bk = first ? (lastq ? K_BWD32ZU : K_BWD32Z) : (lastq ? K_BWD32U : K_BWD32);
-    b.c = common(p, true, 1, 0, 1, bk);
-    b.rec = (const float *)p->recB;
-    b.y = p->y32; b.x = p->d32; b.x64 = lastq ? p->x64 : nullptr;
-    CU(launch(p, bk, b));
+    if ((rc = enqueue_backward(p, bk, (const float *)p->y32, p->d32, lastq ? p->x64 : nullptr))) return rc;
   }
   return SIP_OK;
 }
@@ -353,25 +379,12 @@ int enqueue_iter_f32(sip_plan *p) {
   sip_ctx *ctx = p->ctx;
   if (int rc = enqueue_halo(p)) return rc;
   if (p->nhalo > 0) UTIL(launch_cast_f64_f32(p->beff64, p->r32, p->ncells, ctx->stream));
-  FwdParams<float> f;
-  const int fk = p->sym ? K_FWD32SN : K_FWD32N;
-  f.c = common(p, false, 0, 1, 0, fk);
-  f.rec = (const float *)p->recF;
-  f.rsf = p->rsf;
-  f.b = p->r32;
-  f.x = p->d32;
-  f.y = p->y32;
-  f.partials = p->partials;
-  CU(launch(p, fk, f));
-  UTIL(launch_finalize(p->partials, p->ntiles, p->ctl, p->hist, p->hist_cap, p->status, FIN_RELRES, ctx->stream));
-  BwdParams<float> b;
-  b.c = common(p, true, 1, 0, 1, K_BWD32);
-  b.rec = (const float *)p->recB;
-  b.y = p->y32;
-  b.x = p->d32;
-  b.x64 = nullptr;
-  CU(launch(p, K_BWD32, b));
-  return SIP_OK;
+  if (int rc = enqueue_resid(p, K_RES32N, (const float *)p->recA, (const float *)p->r32, (const float *)p->d32,
+                             p->y32, true))
+    return rc;
+  if (int rc = enqueue_relres(p)) return rc;
+  if (int rc = enqueue_forward(p, K_FWD32, (const float *)p->y32, p->y32)) return rc;
+  return enqueue_backward(p, K_BWD32, (const float *)p->y32, p->d32, (double *)nullptr);
 }
 
 int enqueue_iter(sip_plan *p) {
@@ -461,13 +474,11 @@ int end_sequence(sip_plan *p) {
   return SIP_OK;
 }
 
-// kernels a plan of the given mode launches
-std::vector<int> plan_kinds(int mode, bool sym, bool a32in) {
-  if (mode == SIP_MODE_F64) return {K_FACTOR, sym ? K_FWD64S : K_FWD64, K_BWD64};
-  if (mode == SIP_MODE_F32) return {K_FACTOR32, sym ? K_FWD32SN : K_FWD32N, K_BWD32};
-  std::vector<int> k = {K_FACTOR32, K_FWD32Z, sym ? K_FWD32S : K_FWD32, K_BWD32, K_BWD32Z, K_BWD32U, K_BWD32ZU};
-  k.push_back(a32in ? (sym ? K_RES32AS : K_RES32A) : (sym ? K_RES64S : K_RES64));
-  return k;
+// sweep kernels a plan of the given mode launches
+std::vector<int> plan_kinds(int mode) {
+  if (mode == SIP_MODE_F64) return {K_FACTOR, K_FWD64, K_BWD64};
+  if (mode == SIP_MODE_F32) return {K_FACTOR32, K_FWD32, K_BWD32};
+  return {K_FACTOR32, K_FWD32, K_BWD32, K_BWD32Z, K_BWD32U, K_BWD32ZU};
 }
 
 // Tile shape: rows per thread Q and warps NW (tile = 32 x Q*NW).  Prefer the
@@ -512,7 +523,7 @@ ShapeChoice choose_shape(sip_ctx *ctx, const std::vector<BlockHost> &blocks, con
         if (bcap < 1) { ok = false; break; }
         c.R[kind] = bR;
         c.cap[kind] = bcap;
-        if (kernel_is_ticketed(kind)) capmin = std::min(capmin, bcap);
+        capmin = std::min(capmin, bcap);
       }
       if (!ok) continue;
       const bool onewave = capmin >= ntiles;
@@ -658,7 +669,7 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     bh.n = (long long)bh.d.nx * bh.d.ny * bh.d.nz;
     p->tab_ints = std::max(p->tab_ints, (int)(bh.PO.size() + bh.F.size()));
   }
-  const std::vector<int> kinds = plan_kinds(p->mode, sym, p->a32in);
+  const std::vector<int> kinds = plan_kinds(p->mode);
   const ShapeChoice sc = choose_shape(ctx, p->blocks, kinds, p->tab_ints, opt.tile_k, opt.stages);
   if (sc.Q == 0) {
     delete p;
@@ -695,6 +706,8 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     db.face_tile_words = (long long)db.nsteps_max * (kTJ + p->TK) * kFaceWordsMax;
     db.lo_blk = db.hi_blk = -1;
     db.lo_nj = db.lo_nk = db.hi_nj = db.hi_nk = 0;
+    db.row0 = p->nrows;
+    p->nrows += (long long)db.nz * (db.nx + db.ny - 1);
     const int nt = db.nTJ * db.nTK;
     p->ntiles += nt;
     face0 += (long long)nt * db.face_tile_words;
@@ -729,13 +742,28 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
   } while (0)
   const long long N = ncells;
   const bool f64 = p->mode == SIP_MODE_F64;
-  p->rsf = fwd_rec_values(sym);
+  {
+    // row-parallel launches: every SM filled with the plan's most demanding
+    // residual variant, no more CTAs than 8-row groups
+    int occ = 0;
+    if (f64) {
+      occ = resrow_max_active<double, double, double>(sym, true);
+    } else {
+      occ = resrow_max_active<float, float, float>(sym, p->mode == SIP_MODE_F32);
+      if (p->mode == SIP_MODE_F32_REFINED)
+        occ = std::min(occ, p->a32in ? resrow_max_active<float, double, float>(sym, true)
+                                     : resrow_max_active<double, double, float>(sym, true));
+    }
+    const int wpc = row_threads() / 32;
+    const long long groups = (p->nrows + wpc - 1) / wpc;
+    p->rowgrid = (int)std::max(1ll, std::min<long long>((long long)ctx->nsm * std::max(occ, 1), groups));
+  }
   PA(p->d_tab, tab_total);
   PA(p->d_blocks, nblocks);
   PA(p->d_tiles_f, p->ntiles);
   PA(p->d_tiles_b, p->ntiles);
   PA(p->faces, face0);
-  PA(p->partials, p->ntiles);
+  PA(p->partials, p->rowgrid);
   PA(p->bparts, p->nbparts);
   PA(p->ctl, 1);
   p->hist_cap = 1 << 20;
@@ -751,23 +779,28 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
   PA(p->x64, N);
   double *a7 = nullptr;
   PA(a7, N * 8);
+  const int na = a_rec_values(sym);
   if (f64) {
-    double *rf = nullptr, *rb = nullptr;
-    PA(rf, N * p->rsf);
+    double *rf = nullptr, *rb = nullptr, *ra = nullptr;
+    PA(rf, N * 4);
     PA(rb, N * 4);
+    PA(ra, N * na);
     p->recF = rf;
     p->recB = rb;
+    p->recA = ra;
     PA(p->y64, N);
   } else {
-    float *rf = nullptr, *rb = nullptr;
-    PA(rf, N * p->rsf);
+    float *rf = nullptr, *rb = nullptr, *ra = nullptr;
+    PA(rf, N * 4);
     PA(rb, N * 4);
+    PA(ra, N * na);
     p->recF = rf;
     p->recB = rb;
+    p->recA = ra;
     PA(p->r32, N);
     PA(p->d32, N);
     PA(p->y32, N);
-    if (!p->a32in && p->mode == SIP_MODE_F32_REFINED) PA(p->arec64, N * (sym ? 4 : 8));
+    if (!p->a32in && p->mode == SIP_MODE_F32_REFINED) PA(p->arec64, N * na);
   }
   {
     cudaError_t e = cudaMallocHost(&p->h_ctl, 3 * sizeof(Ctl));
@@ -844,24 +877,24 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->tickets, 0, 4 * sizeof(int), st);
     const size_t es = f64 ? 8 : 4;
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->recF, 0, (size_t)N * p->rsf * es, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->recF, 0, (size_t)N * 4 * es, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->recB, 0, (size_t)N * 4 * es, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->recA, 0, (size_t)N * na * es, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a7, 0, (size_t)N * 8 * sizeof(double), st);
-    if (e == cudaSuccess && p->arec64) e = cudaMemsetAsync(p->arec64, 0, (size_t)N * (sym ? 4 : 8) * 8, st);
+    if (e == cudaSuccess && p->arec64) e = cudaMemsetAsync(p->arec64, 0, (size_t)N * na * 8, st);
     // host vectors must outlive the async copies
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bail(e, "plan upload");
   }
   // A into the plan: the factorisation input (all seven entries, FP64), the
-  // sweep records' A part and, in the refined mode, the FP64 A of the outer
-  // residual.  Coefficients that point out of their block are zeroed.
+  // A records of the residual in the sweep precision and, in the refined
+  // mode with FP64 coefficients, the FP64 A of the outer residual.
+  // Coefficients that point out of their block are zeroed.
   {
     static const int zface[7] = {0, 1, 2, 3, 4, 5, 6};          // ap aw ae as an ab at
     static const int shift_src[7] = {-1, 2, -1, 4, -1, 6, -1};  // symmetric: aw<-ae, as<-an, ab<-at
     static const int shift_axis[7] = {0, 1, 0, 2, 0, 3, 0};
-    // slot of entry q in the forward record / the FP64 A record (-1: not stored)
-    const int fslot_s[7] = {RECS_AP, -1, RECS_AE, -1, RECS_AN, -1, RECS_AT};
-    const int fslot_g[7] = {RECG_AP, RECG_AW, RECG_AE, RECG_AS, RECG_AN, RECG_AB, RECG_AT};
+    // slot of entry q in the A records (-1: not stored)
     const int aslot_s[7] = {0, -1, 1, -1, 2, -1, 3};
     const int aslot_g[7] = {0, 1, 2, 3, 4, 5, 6};
     for (auto &bh : p->blocks) {
@@ -876,11 +909,9 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
         }
         const int zf = sh ? 0 : zface[q];
         cudaError_t e = launch_to_records(s, cd, a7, 0, 8, q, bh.db, zf, sh, st);
-        const int fs = sym ? fslot_s[q] : fslot_g[q];
-        if (e == cudaSuccess && fs >= 0) e = launch_to_records(s, cd, p->recF, f64 ? 0 : 1, p->rsf, fs, bh.db, zf, sh, st);
         const int as = sym ? aslot_s[q] : aslot_g[q];
-        if (e == cudaSuccess && p->arec64 && as >= 0)
-          e = launch_to_records(s, cd, p->arec64, 0, sym ? 4 : 8, as, bh.db, zf, sh, st);
+        if (e == cudaSuccess && as >= 0) e = launch_to_records(s, cd, p->recA, f64 ? 0 : 1, na, as, bh.db, zf, sh, st);
+        if (e == cudaSuccess && p->arec64 && as >= 0) e = launch_to_records(s, cd, p->arec64, 0, na, as, bh.db, zf, sh, st);
         if (e != cudaSuccess) return bail(e, "reorder A");
       }
     }
@@ -895,7 +926,6 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
       fp.a7 = a7;
       fp.recF = (double *)p->recF;
       fp.recB = (double *)p->recB;
-      fp.rsf = p->rsf;
       fp.alpha = opt.alpha;
       e = launch(p, K_FACTOR, fp);
     } else {
@@ -904,7 +934,6 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
       fp.a7 = a7;
       fp.recF = (float *)p->recF;
       fp.recB = (float *)p->recB;
-      fp.rsf = p->rsf;
       fp.alpha = opt.alpha;
       e = launch(p, K_FACTOR32, fp);
     }
@@ -1000,7 +1029,7 @@ int sip_export_factors(sip_plan *p, int blk, double *const out[7]) {
   sip_ctx *ctx = p->ctx;
   for (int q = 0; q < 7; ++q)
     if (!out[q]) return fail(ctx, SIP_ERR_INVALID_ARG, "null output");
-  CU(launch_export_factors(p->recF, p->recB, p->mode == SIP_MODE_F64 ? 0 : 1, p->rsf, out, p->blocks[blk].db,
+  CU(launch_export_factors(p->recF, p->recB, p->mode == SIP_MODE_F64 ? 0 : 1, out, p->blocks[blk].db,
                            ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
   return SIP_OK;
@@ -1120,10 +1149,9 @@ int sip_launch_count(sip_plan *p, int64_t *count_out) {
 }
 
 const char *sip_kernel_name(int kind) {
-  static const char *names[] = {"factor", "fwd64", "fwd64_sym", "bwd64", "fwd32", "fwd32_sym", "fwd32_x0",
-                                "fwd32_norm", "fwd32_sym_norm", "bwd32", "bwd32_x0", "bwd32_upd64",
-                                "bwd32_x0_upd64", "resid64", "resid64_sym", "resid64_a32", "resid64_a32_sym",
-                                "factor32", "utility"};
+  static const char *names[] = {"factor",      "fwd64",    "bwd64",        "factor32",     "fwd32",
+                                "bwd32",       "bwd32_x0", "bwd32_upd64",  "bwd32_x0_upd64", "resid64",
+                                "resid32",     "resid32_norm", "resid64_r32", "utility"};
   static_assert(sizeof(names) / sizeof(names[0]) == K_NKINDS + 1, "kernel names");
   if (kind < 0 || kind > K_NKINDS) return nullptr;
   return names[kind];

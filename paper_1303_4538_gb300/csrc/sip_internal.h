@@ -15,16 +15,15 @@ constexpr int kTJ = 32;           // j extent of a column tile = one warp's lane
 constexpr int kFaceWordsMax = 6;  // 3 FP64 values (the factorisation's UN, UE, UT)
 
 // Per-cell records of a plan (arrays of structs, 16-byte aligned):
-//   forward record  [LB LW LS 1/LP | AP AE AN AT]                   (symmetric, 8 values)
-//                   [LB LW LS 1/LP | AP AW AE AS AN AB AT 0]        (general, 12 values)
-//   backward record [UE UN UT 0]
-//   A record (FP64 residual of the refinement) [AP AE AN AT] or [AP AW AE AS AN AB AT 0]
-//   A7 record (factorisation input)            [AP AW AE AS AN AB AT 0]
+//   L record [LB LW LS 1/LP]   (forward substitution)
+//   U record [UE UN UT 0]      (backward substitution)
+//   A record [AP AE AN AT] (symmetric) or [AP AW AE AS AN AB AT 0] (general),
+//            in the sweep precision, plus an FP64 copy for the outer residual
+//            of the refinement when the coefficients are FP64
+//   A7 record (factorisation input, FP64) [AP AW AE AS AN AB AT 0]
 constexpr int REC_LB = 0, REC_LW = 1, REC_LS = 2, REC_RLP = 3;
-constexpr int RECS_AP = 4, RECS_AE = 5, RECS_AN = 6, RECS_AT = 7;  // symmetric forward record
-constexpr int RECG_AP = 4, RECG_AW = 5, RECG_AE = 6, RECG_AS = 7, RECG_AN = 8, RECG_AB = 9, RECG_AT = 10;
 constexpr int RECB_UE = 0, RECB_UN = 1, RECB_UT = 2;
-__host__ __device__ constexpr int fwd_rec_values(bool sym) { return sym ? 8 : 12; }
+__host__ __device__ constexpr int a_rec_values(bool sym) { return sym ? 4 : 8; }
 
 // Plane layout of one block.  Plane s = i + j + k holds the cells with that
 // index sum; inside a plane the rows k ascend and inside a row the cells j
@@ -47,6 +46,9 @@ struct DevBlock {
   // face (lo) and the +x face (hi), or -1; overlap rectangle j < nj, k < nk
   int lo_blk, hi_blk;
   int lo_nj, lo_nk, hi_nj, hi_nk;
+  // rows of the row-parallel kernels: the block's plane rows (s, k) are
+  // numbered row0 + k (nx + ny - 1) + (s - k)
+  long long row0;
 };
 
 __host__ __device__ inline int plane_row_base(const int *PO, const int *F, int mmax, int nx, int s, int k) {
@@ -95,11 +97,9 @@ constexpr int kTraceWords = 6;
 template <typename T>
 struct FwdParams {
   SweepCommon c;
-  const T *rec;      // forward records
-  int rsf;           // values per forward record (8 symmetric, 12 general)
-  const T *b, *x;
-  T *y;
-  double *partials;  // per global tile: sum of r^2
+  const T *rec;  // L records
+  const T *r;    // right-hand side of the substitution (the residual)
+  T *y;          // may alias r
 };
 
 template <typename T>
@@ -115,26 +115,30 @@ template <typename TF>
 struct FacParams {
   SweepCommon c;
   const double *a7;  // A7 records
-  TF *recF;          // forward records (L part written)
-  TF *recB;          // backward records (U part written)
-  int rsf;           // values per forward record
+  TF *recF;          // L records
+  TF *recB;          // U records
   double alpha;
 };
 
-template <typename TA>
-struct ResParams {  // FP64 residual r = b - A x of the refinement loop (no recurrence)
+// Residual r = b - A x of every plan cell, one warp per plane row
+// (sip_resrow.cu).  Arithmetic in TX (the iterate's type), A widened from TA.
+template <typename TA, typename TX, typename TR>
+struct RowParams {
   const DevBlock *blocks;
-  const Tile *tiles;
-  int ntiles;
-  int tab_ints;
-  Ctl *ctl;
-  int *status;
-  const TA *arec;   // A part of the records: [AP AE AN AT] or [AP AW AE AS AN AB AT 0]
-  int astride;      // values between consecutive cells' A parts
-  const double *b, *x;
-  float *r32;
-  double *partials;
+  int nblocks;
+  long long nrows;    // rows of all blocks
+  const Ctl *ctl;     // done: the kernel does nothing
+  const int *status;  // not DEV_OK: the kernel does nothing
+  const TA *arec;     // A records: [AP AE AN AT] (symmetric) or [AP AW AE AS AN AB AT 0] per cell
+  const TX *b, *x;
+  TR *r;
+  double *partials;  // per CTA sum of r^2 (nullptr: no norm)
 };
+int row_threads();
+template <typename TA, typename TX, typename TR>
+cudaError_t launch_resrow(const RowParams<TA, TX, TR> &prm, bool sym, int grid, cudaStream_t st);
+template <typename TA, typename TX, typename TR>
+int resrow_max_active(bool sym, bool norm);
 
 // utilities (sip_util.cu)
 cudaError_t launch_to_records(const void *src, int src_is_f32, void *dst, int dst_is_f32, int stride, int slot,
@@ -148,8 +152,8 @@ cudaError_t launch_finalize(const double *partials, int n, Ctl *ctl, double *his
 cudaError_t launch_set_ctl(Ctl *ctl, double rtol, int max_iters, cudaStream_t st);
 cudaError_t launch_cast_f64_f32(const double *src, float *dst, long long n, cudaStream_t st);
 cudaError_t launch_cast_f32_f64(const float *src, double *dst, long long n, cudaStream_t st);
-cudaError_t launch_export_factors(const void *recF, const void *recB, int is_f32, int rsf,
-                                  double *const out[7], const DevBlock &hb, cudaStream_t st);
+cudaError_t launch_export_factors(const void *recF, const void *recB, int is_f32, double *const out[7],
+                                  const DevBlock &hb, cudaStream_t st);
 
 // Natural-layout block for the residual norm (sip_resnorm.cu).  a[] = AP, AW,
 // AE, AS, AN, AB, AT (double or float); symmetric: AW/AS/AB are not read.

@@ -1,5 +1,6 @@
-// sip_k32.cu -- instantiations of the FP32 sweep kernels (inner iterations of
-// the mixed-precision refinement and the pure single-precision relaxation).
+// sip_k32.cu -- instantiations of the FP32 sweep kernels (factorisation with
+// FP32 factors, inner iterations of the mixed-precision refinement and the
+// pure single-precision relaxation).
 #include "sip_kernels.h"
 #include "sip_sweeps.cuh"
 
@@ -8,11 +9,8 @@ namespace sipk {
 template <int Q, int R>
 static const void *pick32(int kind) {
   switch (kind) {
-    case K_FWD32: return (const void *)k_forward<float, false, false, false, Q, R>;
-    case K_FWD32S: return (const void *)k_forward<float, true, false, false, Q, R>;
-    case K_FWD32Z: return (const void *)k_forward<float, false, true, false, Q, R>;
-    case K_FWD32N: return (const void *)k_forward<float, false, false, true, Q, R>;
-    case K_FWD32SN: return (const void *)k_forward<float, true, false, true, Q, R>;
+    case K_FACTOR32: return (const void *)k_factor<float, Q, R>;
+    case K_FWD32: return (const void *)k_forward<float, Q, R>;
     case K_BWD32: return (const void *)k_backward<float, false, false, Q, R>;
     case K_BWD32Z: return (const void *)k_backward<float, true, false, Q, R>;
     case K_BWD32U: return (const void *)k_backward<float, false, true, Q, R>;

@@ -1,5 +1,5 @@
 // sip_k64.cu -- instantiations of the FP64 sweep kernels (factorisation with
-// FP64 factors, FP64 forward / backward).
+// FP64 factors, FP64 forward / backward substitution).
 #include "sip_kernels.h"
 #include "sip_sweeps.cuh"
 
@@ -9,8 +9,7 @@ template <int Q, int R>
 static const void *pick64(int kind) {
   switch (kind) {
     case K_FACTOR: return (const void *)k_factor<double, Q, R>;
-    case K_FWD64: return (const void *)k_forward<double, false, false, true, Q, R>;
-    case K_FWD64S: return (const void *)k_forward<double, true, false, true, Q, R>;
+    case K_FWD64: return (const void *)k_forward<double, Q, R>;
     case K_BWD64: return (const void *)k_backward<double, false, false, Q, R>;
     default: return nullptr;
   }

@@ -7,37 +7,34 @@
 namespace sipk {
 
 enum KernelKind {
+  // wavefront sweeps (ticketed; addressed by Q and R)
   K_FACTOR = 0,   // Stone factorisation, FP64 factors
-  K_FWD64,        // FP64 residual + norm + forward substitution, general A
-  K_FWD64S,       // same, symmetric A (Listing 1 residual)
+  K_FWD64,        // FP64 forward substitution y = L^-1 r
   K_BWD64,        // FP64 backward substitution + update
-  K_FWD32,        // FP32 forward, general, no norm (inner refinement sweeps)
-  K_FWD32S,       // FP32 forward, symmetric, no norm
-  K_FWD32Z,       // FP32 forward with x = 0 (r = b)
-  K_FWD32N,       // FP32 forward, general, with norm (pure single-precision mode)
-  K_FWD32SN,      // FP32 forward, symmetric, with norm
+  K_FACTOR32,     // Stone factorisation (FP64 arithmetic), FP32 factors
+  K_FWD32,        // FP32 forward substitution
   K_BWD32,        // FP32 backward + update
   K_BWD32Z,       // FP32 backward with x = 0 on entry
   K_BWD32U,       // FP32 backward + update, then x64 += x
   K_BWD32ZU,      // x = 0 on entry, then x64 += x
-  K_RES64,        // FP64 residual of the refinement loop, A in FP64
-  K_RES64S,       // same, symmetric
-  K_RES32A,       // FP64 residual, A stored in FP32 (widened)
-  K_RES32AS,      // same, symmetric
-  K_FACTOR32,     // Stone factorisation (FP64 arithmetic), FP32 factors
+  // row-parallel residual r = b - A x (sip_resrow.cu; not ticketed, no Q/R)
+  K_RES64,        // FP64: r into the substitution buffer, with the norm
+  K_RES32,        // FP32, no norm (inner iterations of the refinement)
+  K_RES32N,       // FP32 with the norm (single-precision mode)
+  K_RES64R,       // FP64 residual of the refinement (A in FP64 or FP32), r rounded to FP32, norm
   K_NKINDS
 };
+constexpr bool kind_is_row(int kind) { return kind >= K_RES64 && kind < K_NKINDS; }
 
 constexpr int kQs[2] = {2, 4};
 constexpr int kRs[2] = {4, 6};
 
+// sweep kernel of a kind (nullptr for the row kinds)
 const void *kernel_ptr(int kind, int Q, int R);
-// dynamic shared memory of a launch with `nthreads` threads per CTA
+// dynamic shared memory of a sweep launch with `nthreads` threads per CTA
 size_t kernel_smem(int kind, int Q, int R, int nthreads, int tab_ints);
-bool kernel_is_ticketed(int kind);
 
 const void *kernel_ptr_64(int kind, int Q, int R);
 const void *kernel_ptr_32(int kind, int Q, int R);
-const void *kernel_ptr_res(int kind, int Q, int R);
 
 }  // namespace sipk

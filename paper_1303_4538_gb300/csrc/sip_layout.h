@@ -4,7 +4,7 @@
 // Every sweep kernel's dynamic shared memory is
 //   [ PO + F tables of the current block ]
 //   [ R stages: per step the staged records of the thread's Q rows, then
-//     scalar slots (rhs, x of the next cell, halo values) ]
+//     scalar slots (r; y and x; the FP64 iterate of the refinement) ]
 //   [ exchange between neighbouring warps, double buffered ]
 //   [ R stages of face records consumed by the tile's edge threads ]
 #pragma once
@@ -18,7 +18,7 @@ struct SweepLayout {
   size_t tab;    // bytes of the PO/F tables
   size_t step;   // bytes of one stage
   size_t rec;    // bytes of the staged records inside a stage (Q * NT * rsb)
-  size_t aux;    // bytes of an auxiliary 8-byte region after the records (x64 or FP64 scalars)
+  size_t aux;    // bytes of an auxiliary 8-byte region after the records (x64)
   size_t exch;   // bytes of the exchange area
   size_t faces;  // bytes of the face ring
   size_t total;
@@ -27,19 +27,19 @@ struct SweepLayout {
   int fs;        // face slots per stage (TK + 32)
 };
 
-// forward sweep (esize: 4 or 8; zx: x = 0)
-__host__ __device__ inline SweepLayout fwd_layout(int esize, bool sym, bool zx, int Q, int R, int NT, int tab_ints) {
+// forward sweep (esize: 4 or 8): L record [LB LW LS 1/LP] and r per row;
+// the exchange carries y of a warp's last row
+__host__ __device__ inline SweepLayout fwd_layout(int esize, int Q, int R, int NT, int tab_ints) {
   SweepLayout L{};
   const int NW = NT / 32, TK = NW * Q;
-  L.rsb = (zx ? 4 : (sym ? 8 : 12)) * esize;
-  L.nsv = zx ? Q : Q * (sym ? 4 : 3) + (sym ? 3 : 2);
-  const int neb = zx ? 1 : (sym ? 3 : 2), nexT = zx ? 0 : 1;
+  L.rsb = 4 * esize;
+  L.nsv = Q;
   L.fs = TK + 32;
   L.tab = lay_a16((size_t)tab_ints * 4);
   L.rec = (size_t)Q * NT * L.rsb;
   L.aux = 0;
   L.step = lay_a16(L.rec + (size_t)L.nsv * NT * esize);
-  L.exch = lay_a16((size_t)(2 * neb + 2 * nexT) * NW * 32 * esize);
+  L.exch = lay_a16((size_t)2 * NW * 32 * esize);
   L.faces = (size_t)R * L.fs * 2 * 8;
   L.total = L.tab + (size_t)R * L.step + L.exch + L.faces;
   return L;
@@ -76,26 +76,6 @@ __host__ __device__ inline SweepLayout fac_layout(int Q, int R, int NT, int tab_
   L.exch = lay_a16((size_t)2 * 3 * NW * 32 * 8);
   L.faces = (size_t)R * L.fs * 6 * 8;
   L.total = L.tab + (size_t)R * L.step + L.exch + L.faces;
-  return L;
-}
-
-// FP64 residual: A part (asize 4 or 8) per row; FP64 scalars b, x(i+1), halo
-// x per row plus the two k halos; for symmetric A the halo AN/AT (asize each)
-__host__ __device__ inline SweepLayout res_layout(int asize, bool sym, int Q, int R, int NT, int tab_ints) {
-  SweepLayout L{};
-  const int NW = NT / 32;
-  L.rsb = (sym ? 4 : 8) * asize;
-  L.nsv = 3 * Q + 2;  // FP64 slots
-  L.fs = 0;
-  L.tab = lay_a16((size_t)tab_ints * 4);
-  L.rec = (size_t)Q * NT * L.rsb;
-  L.aux = lay_a16((size_t)L.nsv * NT * 8);
-  const size_t halo_a = sym ? lay_a16((size_t)(Q + 1) * NT * asize) : 0;
-  L.step = lay_a16(L.rec) + L.aux + halo_a;
-  const int neb = sym ? 2 : 1;
-  L.exch = lay_a16((size_t)(2 * neb + 2) * NW * 32 * 8);
-  L.faces = 0;
-  L.total = L.tab + (size_t)R * L.step + L.exch;
   return L;
 }
 

@@ -1,9 +1,11 @@
 // sip_sweeps.cuh -- sm_103a kernels of Stone's SIP over the plane layout.
 //
 // The recurrences of the method (arXiv:1303.4538, Sec. 1 / Sec. 4.1: lu3d,
-// resforward3d, backward3d) make a cell depend on its lower neighbours W, S,
-// B (factorisation and forward substitution) or on its upper neighbours E, N,
-// T (backward substitution).  All cells of one hyperplane i + j + k = s are
+// the substitution part of resforward3d, backward3d) make a cell depend on
+// its lower neighbours W, S, B (factorisation and forward substitution) or on
+// its upper neighbours E, N, T (backward substitution).  The residual part of
+// resforward3d has no recurrence and runs in the row-parallel kernel of
+// sip_resrow.cu.  All cells of one hyperplane i + j + k = s are
 // independent, so the sweeps advance plane by plane.  Work decomposition:
 //
 //   * the (j, k) cross-section of a block is cut into 32 x TK column tiles;
@@ -14,9 +16,10 @@
 //     registers, S/N from lanes j -+ 1 by warp shuffles, B/T from the
 //     thread's own neighbouring row, and across warps through a
 //     double-buffered shared-memory exchange (one barrier per step);
-//   * each cell's static data (coefficients and factors) is one 16-byte
-//     aligned record, staged with cp.async.cg (L2 only) R-1 steps ahead into a
-//     ring of shared-memory stages together with the rhs and x values; invalid
+//   * each cell's static data (factors, or A for the factorisation) is one
+//     16-byte aligned record, staged with cp.async.cg (L2 only) R-1 steps
+//     ahead into a ring of shared-memory stages together with the cell's
+//     values (r; y and x for the backward sweep); invalid
 //     cells are zero-filled, so the arithmetic runs without branches and
 //     inactive threads produce zeros;
 //   * row addresses come from two small per-block tables held in shared
@@ -214,22 +217,6 @@ __device__ __forceinline__ unsigned sweep_prologue(const SweepCommon &c) {
     c.ctl->epochs[c.ep_slot ^ 1] = ep + 1u;
   }
   return ep;
-}
-
-__device__ __forceinline__ double block_sum(double v, double *s_red) {
-  // deterministic: fixed shuffle tree, then warps summed in order by thread 0
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) s_red[wid] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int q = 0; q < nw; ++q) t += s_red[q];
-  }
-  __syncthreads();
-  return t;
 }
 
 // Copy the block's PO and F tables into shared memory when the CTA moves to a
@@ -451,7 +438,7 @@ __global__ void __launch_bounds__(512) k_factor(FacParams<TF> P) {
               !isfinite(UN) || !isfinite(UE) || !isfinite(UT) || !isfinite(LP))
             atomicCAS(c.status, DEV_OK, DEV_BREAKDOWN);
           const long long cell = B.cell0 + rb(g.s0 + t, g.k(q)) + g.j;
-          TF *fr = P.recF + cell * P.rsf;
+          TF *fr = P.recF + cell * 4;
           fr[REC_LB] = (TF)LB;
           fr[REC_LW] = (TF)LW;
           fr[REC_LS] = (TF)LS;
@@ -492,24 +479,18 @@ __global__ void __launch_bounds__(512) k_factor(FacParams<TF> P) {
 }
 
 // ============================================================ forward sweep
-// resforward3d: r = b - A x (norm of r), then y = L^{-1} r with
-//   y_P = (r_P - LB y_B - LW y_W - LS y_S) * (1/LP).
-// SYM: A symmetric, only AP, AE, AN, AT are stored; AW(P) = AE(W),
-//      AS(P) = AN(S), AB(P) = AT(B) (the paper's Listing 1).
-// ZX:  x = 0, so r = b (first inner iteration of the refinement).
-template <typename T, bool SYM, bool ZX, bool NORM, int Q, int R>
+// The substitution half of resforward3d: y = L^{-1} r with
+//   y_P = (r_P - LB y_B - LW y_W - LS y_S) * (1/LP),  ascending planes.
+// The residual r = b - A x (and its norm) is computed beforehand by the
+// row-parallel kernel, so the wavefront carries only this recurrence.  r and y
+// may alias (in place): a cell's r is staged before its y is stored, and no
+// other cell reads it.
+template <typename T, int Q, int R>
 __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
-  static_assert(!(SYM && ZX), "x = 0 needs no matrix");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_claim, s_blk;
-  __shared__ double s_red[32];
   constexpr int W = 2;
-  constexpr int RSS = ZX ? 4 : fwd_rec_values(SYM);  // staged values per record (from its start)
-  constexpr int NCP = RSS * (int)sizeof(T) / 16;
-  // scalar slots: per row b, x(i+1), halo x (j), halo AN (j, symmetric); then halo x (k below / above), halo AT
-  constexpr int SB = 0, SXP = Q, SHJ = 2 * Q, SHA = 3 * Q;
-  constexpr int SHKB = SYM ? 4 * Q : 3 * Q, SHKT = SHKB + 1, SHAB = SHKB + 2;
-  constexpr int AO_AP = SYM ? RECS_AP : RECG_AP;
+  constexpr int NCP = 4 * (int)sizeof(T) / 16;  // 16-byte copies per L record
   const SweepCommon &c = P.c;
   const unsigned ep = sweep_prologue(c);
   if (threadIdx.x == 0) s_blk = -1;
@@ -517,11 +498,10 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
   if (__syncthreads_or(c.ctl->done || ld_relaxed(c.status) != DEV_OK)) return;
   const unsigned expect = ep + (c.stall ? 0x40000000u : 0u);
   const int NT = blockDim.x, tid = threadIdx.x;
-  const SweepLayout L = fwd_layout((int)sizeof(T), SYM, ZX, Q, R, NT, c.tab_ints);
+  const SweepLayout L = fwd_layout((int)sizeof(T), Q, R, NT, c.tab_ints);
   int *sPO = reinterpret_cast<int *>(smem_raw);
   unsigned char *stage = smem_raw + L.tab;
-  constexpr int NEB = ZX ? 1 : (SYM ? 3 : 2);  // published by a warp's last row: ym1, xm1, atm1
-  T *exB = reinterpret_cast<T *>(stage + (size_t)R * L.step);  // [2][NEB][NW][32]
+  T *exB = reinterpret_cast<T *>(stage + (size_t)R * L.step);  // [2][NW][32]: y of a warp's last row
   uint64_t *fst = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(exB) + L.exch);
   const int FS = L.fs;
   bool abort = false;
@@ -536,7 +516,6 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
     const int *sF = sPO + B.nplanes;
     const Geo<Q> g(B, tl);
     const int NW = g.NW, lane = g.lane, w = g.w;
-    T *exT = exB + (size_t)2 * NEB * NW * 32;  // [2][NW][32]
     uint64_t *myf = tile_faces(c, B, tl.gtile);
     uint64_t *upJ = g.hasS ? tile_faces(c, B, tl.gtile - 1) : nullptr;
     uint64_t *upK = g.hasB ? tile_faces(c, B, tl.gtile - B.nTJ) : nullptr;
@@ -556,41 +535,13 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           const int i = g.i(tt, q);
-          const bool colq = g.col(B, q);
-          const bool v = colq && i >= 0 && i < B.nx;
+          const bool v = g.col(B, q) && i >= 0 && i < B.nx;
           const long long a = v ? B.cell0 + rb(s, g.k(q)) + g.j : 0;
-          unsigned char *d = st + ((size_t)q * NT + tid) * (RSS * sizeof(T));
-          const unsigned char *src = reinterpret_cast<const unsigned char *>(P.rec + a * P.rsf);
+          unsigned char *d = st + ((size_t)q * NT + tid) * (4 * sizeof(T));
+          const unsigned char *src = reinterpret_cast<const unsigned char *>(P.rec + a * 4);
 #pragma unroll
           for (int z = 0; z < NCP; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v);
-          cp_async_zfill<sizeof(T)>(sc + (SB + q) * NT, P.b + a, v);
-          if constexpr (!ZX) {
-            const bool vp = colq && i + 1 >= 0 && i + 1 < B.nx;
-            const long long ap1 = vp ? B.cell0 + rb(s + 1, g.k(q)) + g.j : 0;
-            cp_async_zfill<sizeof(T)>(sc + (SXP + q) * NT, P.x + ap1, vp);
-            long long hj = 0;
-            bool vj = false;
-            if (lane == 0 && g.hasS && v) {
-              hj = B.cell0 + rb(s - 1, g.k(q)) + g.j0 - 1;
-              vj = true;
-            } else if (lane == kTJ - 1 && g.hasN && v) {
-              hj = B.cell0 + rb(s + 1, g.k(q)) + g.j0 + kTJ;
-              vj = true;
-            }
-            cp_async_zfill<sizeof(T)>(sc + (SHJ + q) * NT, P.x + hj, vj);
-            if constexpr (SYM) cp_async_zfill<sizeof(T)>(sc + (SHA + q) * NT, P.rec + hj * P.rsf + RECS_AN, vj && lane == 0);
-            if (q == 0 && g.eB) {
-              const bool vb = g.hasB && v;
-              const long long hk = vb ? B.cell0 + rb(s - 1, g.k0 - 1) + g.j : 0;
-              cp_async_zfill<sizeof(T)>(sc + SHKB * NT, P.x + hk, vb);
-              if constexpr (SYM) cp_async_zfill<sizeof(T)>(sc + SHAB * NT, P.rec + hk * P.rsf + RECS_AT, vb);
-            }
-            if (q == Q - 1 && g.eT) {
-              const bool vt = g.hasT && v;
-              const long long hk = vt ? B.cell0 + rb(s + 1, g.k0 + g.TK) + g.j : 0;
-              cp_async_zfill<sizeof(T)>(sc + SHKT * NT, P.x + hk, vt);
-            }
-          }
+          cp_async_zfill<sizeof(T)>(sc + q * NT, P.r + a, v);
           if (lane == 0 && g.hasS && v) rec_prefetch<W>(fs + g.dk(q) * W, faceJ(upJ, B, tt + kTJ - 1, g.dk(q), W));
           if (q == 0 && g.eB && g.hasB && v)
             rec_prefetch<W>(fs + (g.TK + lane) * W, faceK(upK, B, tt + g.TK - 1, lane, W));
@@ -601,32 +552,17 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
 #pragma unroll
     for (int tt = 0; tt < R - 1; ++tt) issue(tt);
 
-    T xm1[Q], x0[Q], ym1[Q], aem1[Q], anm1[Q], atm1[Q];
+    T ym1[Q];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) xm1[q] = x0[q] = ym1[q] = aem1[q] = anm1[q] = atm1[q] = T(0);
-    double acc = 0.0;
-    // x of a column's first cell normally arrives as the previous step's x(i+1);
-    // the tile's corner column starts at i = 0 on step 0, so it reads it here
-    if constexpr (!ZX) {
-      if (lane == 0 && w == 0 && g.col(B, 0)) x0[0] = P.x[B.cell0 + rb(g.s0, g.k0) + g.j];
-    }
+    for (int q = 0; q < Q; ++q) ym1[q] = T(0);
     for (int t = 0; t < g.nsteps; ++t) {
       issue(t + R - 1);
       cp_async_wait<R - 1>();
       const unsigned char *st = stage + (size_t)(t % R) * L.step;
       const T *sc = reinterpret_cast<const T *>(st + L.rec) + tid;
       const uint64_t *fs = fst + (size_t)(t % R) * FS * W;
-      const int buf = t & 1;
-      T xp1[Q];
-#pragma unroll
-      for (int q = 0; q < Q; ++q) xp1[q] = ZX ? T(0) : sc[(SXP + q) * NT];
-      T *E = exB + (size_t)buf * NEB * NW * 32;
-      E[(0 * NW + w) * 32 + lane] = ym1[Q - 1];
-      if constexpr (!ZX) {
-        E[(1 * NW + w) * 32 + lane] = xm1[Q - 1];
-        if constexpr (SYM) E[(2 * NW + w) * 32 + lane] = atm1[Q - 1];
-        exT[((size_t)buf * NW + w) * 32 + lane] = xp1[0];
-      }
+      T *E = exB + (size_t)(t & 1) * NW * 32;
+      E[w * 32 + lane] = ym1[Q - 1];
       T yK = T(0);
       if (g.eB) {
         const int i0 = g.i(t, 0);
@@ -642,8 +578,8 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
       for (int q = 0; q < Q; ++q) {
         const int i = g.i(t, q);
         const bool act = g.col(B, q) && i >= 0 && i < B.nx;
-        const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * (RSS * sizeof(T)));
-        T r = sc[(SB + q) * NT];
+        const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * (4 * sizeof(T)));
+        const T r = sc[q * NT];
         T yS = shfl_up1(ym1[q]);
         if (lane == 0) {
           yS = T(0);
@@ -655,50 +591,12 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
         }
         T yB;
         if (q > 0) yB = ym1[q > 0 ? q - 1 : 0];
-        else if (w > 0) yB = E[(0 * NW + w - 1) * 32 + lane];
+        else if (w > 0) yB = E[(w - 1) * 32 + lane];
         else yB = yK;
-        if constexpr (!ZX) {
-          T xS = shfl_up1(xm1[q]);
-          T xN = shfl_dn1(xp1[q]);
-          if (lane == 0) xS = sc[(SHJ + q) * NT];
-          if (lane == kTJ - 1) xN = sc[(SHJ + q) * NT];
-          T xB, xT;
-          if (q > 0) xB = xm1[q > 0 ? q - 1 : 0];
-          else if (w > 0) xB = E[(1 * NW + w - 1) * 32 + lane];
-          else xB = sc[SHKB * NT];
-          if (q < Q - 1) xT = xp1[q < Q - 1 ? q + 1 : 0];
-          else if (w < NW - 1) xT = exT[((size_t)buf * NW + w + 1) * 32 + lane];
-          else xT = sc[SHKT * NT];
-          if constexpr (SYM) {
-            const T ap = rec[RECS_AP], ae = rec[RECS_AE], an = rec[RECS_AN], at = rec[RECS_AT];
-            T asv = shfl_up1(anm1[q]);
-            if (lane == 0) asv = sc[(SHA + q) * NT];
-            T abv;
-            if (q > 0) abv = atm1[q > 0 ? q - 1 : 0];
-            else if (w > 0) abv = E[(2 * NW + w - 1) * 32 + lane];
-            else abv = sc[SHAB * NT];
-            r = fma(-ap, x0[q], r);
-            r = fma(-aem1[q], xm1[q], r);
-            r = fma(-ae, xp1[q], r);
-            r = fma(-asv, xS, r);
-            r = fma(-an, xN, r);
-            r = fma(-abv, xB, r);
-            r = fma(-at, xT, r);
-          } else {
-            r = fma(-rec[RECG_AP], x0[q], r);
-            r = fma(-rec[RECG_AW], xm1[q], r);
-            r = fma(-rec[RECG_AE], xp1[q], r);
-            r = fma(-rec[RECG_AS], xS, r);
-            r = fma(-rec[RECG_AN], xN, r);
-            r = fma(-rec[RECG_AB], xB, r);
-            r = fma(-rec[RECG_AT], xT, r);
-          }
-        }
         T y = fma(-rec[REC_LB], yB, r);
         y = fma(-rec[REC_LW], ym1[q], y);
         y = fma(-rec[REC_LS], yS, y);
         y = y * rec[REC_RLP];
-        if constexpr (NORM) acc = fma((double)r, (double)r, acc);
         if (act) {
           const long long a = B.cell0 + rb(g.s0 + t, g.k(q)) + g.j;
           P.y[a] = y;
@@ -707,26 +605,11 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
         }
         ny[q] = act ? y : T(0);
       }
-      // rotate the column state (the last loop read the pre-rotation values)
 #pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        if constexpr (SYM) {
-          const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * (RSS * sizeof(T)));
-          aem1[q] = rec[RECS_AE];
-          anm1[q] = rec[RECS_AN];
-          atm1[q] = rec[RECS_AT];
-        }
-        xm1[q] = x0[q];
-        x0[q] = xp1[q];
-        ym1[q] = ny[q];
-      }
+      for (int q = 0; q < Q; ++q) ym1[q] = ny[q];
     }
     cp_async_wait<0>();
     if (tr && threadIdx.x == 0) tr[2] = gtimer();
-    if constexpr (NORM) {
-      const double tot = block_sum(acc, s_red);
-      if (tid == 0) P.partials[tl.gtile] = tot;
-    }
     __syncthreads();
   }
 }
@@ -877,173 +760,6 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
     }
     cp_async_wait<0>();
     if (tr && threadIdx.x == 0) tr[2] = gtimer();
-    __syncthreads();
-  }
-}
-
-// ======================================================= FP64 residual (refinement)
-// r = b - A x in FP64 arithmetic (A stored as TA, widened), sum r^2 per tile,
-// r32 = (float) r.  No recurrence: every tile is independent.
-template <typename TA, bool SYM, int Q, int R>
-__global__ void __launch_bounds__(512) k_resid(ResParams<TA> P) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_blk;
-  __shared__ double s_red[32];
-  constexpr int NA = SYM ? 4 : 8;  // staged A values per row
-  constexpr int NCP = NA * (int)sizeof(TA) / 16;
-  // FP64 scalar slots: per row b, x(i+1), halo x (j); then halo x below / above
-  constexpr int SB = 0, SXP = Q, SHJ = 2 * Q, SHKB = 3 * Q, SHKT = 3 * Q + 1;
-  // symmetric halo A (TA): per row AN of (i, j0-1, k); AT of (i, j, k0-1)
-  constexpr int AHA = 0, AHB = Q;
-  constexpr int OAE = SYM ? 1 : 2, OAN = SYM ? 2 : 4, OAT = SYM ? 3 : 6;  // in the A part
-  if (threadIdx.x == 0) s_blk = -1;
-  if (__syncthreads_or(P.ctl->done || ld_relaxed(P.status) != DEV_OK)) return;
-  const int NT = blockDim.x, tid = threadIdx.x;
-  const SweepLayout L = res_layout((int)sizeof(TA), SYM, Q, R, NT, P.tab_ints);
-  int *sPO = reinterpret_cast<int *>(smem_raw);
-  unsigned char *stage = smem_raw + L.tab;
-  constexpr int NEB = SYM ? 2 : 1;  // published by a warp's last row: xm1 (atm1)
-  double *exB = reinterpret_cast<double *>(stage + (size_t)R * L.step);  // [2][NEB][NW][32], then exT [2][NW][32]
-  const size_t recb = lay_a16(L.rec);
-
-  for (int m = blockIdx.x; m < P.ntiles; m += gridDim.x) {
-    const Tile tl = P.tiles[m];
-    const DevBlock B = P.blocks[tl.blk];
-    load_tables(B, tl.blk, sPO, &s_blk);
-    const int *sF = sPO + B.nplanes;
-    const Geo<Q> g(B, tl);
-    const int NW = g.NW, lane = g.lane, w = g.w;
-    double *exT = exB + (size_t)2 * NEB * NW * 32;
-    auto rb = [&](int s, int k) { return plane_row_base(sPO, sF, B.mmax, B.nx, s, k); };
-
-    auto issue = [&](int tt) {
-      if (tt < g.nsteps) {
-        const int s = g.s0 + tt;
-        unsigned char *st = stage + (size_t)(tt % R) * L.step;
-        double *sc = reinterpret_cast<double *>(st + recb) + tid;
-        TA *sa = reinterpret_cast<TA *>(st + recb + L.aux) + tid;
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-          const int i = g.i(tt, q);
-          const bool colq = g.col(B, q);
-          const bool v = colq && i >= 0 && i < B.nx;
-          const long long a = v ? B.cell0 + rb(s, g.k(q)) + g.j : 0;
-          unsigned char *d = st + ((size_t)q * NT + tid) * (NA * sizeof(TA));
-          const unsigned char *src = reinterpret_cast<const unsigned char *>(P.arec + a * P.astride);
-#pragma unroll
-          for (int z = 0; z < NCP; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v);
-          cp_async_zfill<8>(sc + (SB + q) * NT, P.b + a, v);
-          const bool vp = colq && i + 1 >= 0 && i + 1 < B.nx;
-          const long long ap1 = vp ? B.cell0 + rb(s + 1, g.k(q)) + g.j : 0;
-          cp_async_zfill<8>(sc + (SXP + q) * NT, P.x + ap1, vp);
-          long long hj = 0;
-          bool vj = false;
-          if (lane == 0 && g.hasS && v) {
-            hj = B.cell0 + rb(s - 1, g.k(q)) + g.j0 - 1;
-            vj = true;
-          } else if (lane == kTJ - 1 && g.hasN && v) {
-            hj = B.cell0 + rb(s + 1, g.k(q)) + g.j0 + kTJ;
-            vj = true;
-          }
-          cp_async_zfill<8>(sc + (SHJ + q) * NT, P.x + hj, vj);
-          if constexpr (SYM)
-            cp_async_zfill<sizeof(TA)>(sa + (AHA + q) * NT, P.arec + hj * P.astride + OAN, vj && lane == 0);
-          if (q == 0 && g.eB) {
-            const bool vb = g.hasB && v;
-            const long long hk = vb ? B.cell0 + rb(s - 1, g.k0 - 1) + g.j : 0;
-            cp_async_zfill<8>(sc + SHKB * NT, P.x + hk, vb);
-            if constexpr (SYM) cp_async_zfill<sizeof(TA)>(sa + AHB * NT, P.arec + hk * P.astride + OAT, vb);
-          }
-          if (q == Q - 1 && g.eT) {
-            const bool vt = g.hasT && v;
-            const long long hk = vt ? B.cell0 + rb(s + 1, g.k0 + g.TK) + g.j : 0;
-            cp_async_zfill<8>(sc + SHKT * NT, P.x + hk, vt);
-          }
-        }
-      }
-      cp_async_commit();
-    };
-#pragma unroll
-    for (int tt = 0; tt < R - 1; ++tt) issue(tt);
-
-    double xm1[Q], x0[Q], aem1[Q], anm1[Q], atm1[Q], acc = 0.0;
-#pragma unroll
-    for (int q = 0; q < Q; ++q) xm1[q] = x0[q] = aem1[q] = anm1[q] = atm1[q] = 0.0;
-    if (lane == 0 && w == 0 && g.col(B, 0)) x0[0] = P.x[B.cell0 + rb(g.s0, g.k0) + g.j];
-    for (int t = 0; t < g.nsteps; ++t) {
-      issue(t + R - 1);
-      cp_async_wait<R - 1>();
-      const unsigned char *st = stage + (size_t)(t % R) * L.step;
-      const double *sc = reinterpret_cast<const double *>(st + recb) + tid;
-      const TA *sa = reinterpret_cast<const TA *>(st + recb + L.aux) + tid;
-      const int buf = t & 1;
-      double xp1[Q];
-#pragma unroll
-      for (int q = 0; q < Q; ++q) xp1[q] = sc[(SXP + q) * NT];
-      double *E = exB + (size_t)buf * NEB * NW * 32;
-      E[(0 * NW + w) * 32 + lane] = xm1[Q - 1];
-      if constexpr (SYM) E[(1 * NW + w) * 32 + lane] = atm1[Q - 1];
-      exT[((size_t)buf * NW + w) * 32 + lane] = xp1[0];
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const int i = g.i(t, q);
-        const bool act = g.col(B, q) && i >= 0 && i < B.nx;
-        const TA *ar = reinterpret_cast<const TA *>(st + ((size_t)q * NT + tid) * (NA * sizeof(TA)));
-        double xS = shfl_up1(xm1[q]);
-        double xN = shfl_dn1(xp1[q]);
-        if (lane == 0) xS = sc[(SHJ + q) * NT];
-        if (lane == kTJ - 1) xN = sc[(SHJ + q) * NT];
-        double xB, xT;
-        if (q > 0) xB = xm1[q > 0 ? q - 1 : 0];
-        else if (w > 0) xB = E[(0 * NW + w - 1) * 32 + lane];
-        else xB = sc[SHKB * NT];
-        if (q < Q - 1) xT = xp1[q < Q - 1 ? q + 1 : 0];
-        else if (w < NW - 1) xT = exT[((size_t)buf * NW + w + 1) * 32 + lane];
-        else xT = sc[SHKT * NT];
-        double r = sc[(SB + q) * NT];
-        if constexpr (SYM) {
-          const double ap = ar[0], ae = ar[OAE], an = ar[OAN], at = ar[OAT];
-          double asv = shfl_up1(anm1[q]);
-          if (lane == 0) asv = (double)sa[(AHA + q) * NT];
-          double abv;
-          if (q > 0) abv = atm1[q > 0 ? q - 1 : 0];
-          else if (w > 0) abv = E[(1 * NW + w - 1) * 32 + lane];
-          else abv = (double)sa[AHB * NT];
-          r = fma(-ap, x0[q], r);
-          r = fma(-aem1[q], xm1[q], r);
-          r = fma(-ae, xp1[q], r);
-          r = fma(-asv, xS, r);
-          r = fma(-an, xN, r);
-          r = fma(-abv, xB, r);
-          r = fma(-at, xT, r);
-        } else {
-          r = fma(-(double)ar[0], x0[q], r);
-          r = fma(-(double)ar[1], xm1[q], r);
-          r = fma(-(double)ar[2], xp1[q], r);
-          r = fma(-(double)ar[3], xS, r);
-          r = fma(-(double)ar[4], xN, r);
-          r = fma(-(double)ar[5], xB, r);
-          r = fma(-(double)ar[6], xT, r);
-        }
-        acc = fma(r, r, acc);
-        if (act) P.r32[B.cell0 + rb(g.s0 + t, g.k(q)) + g.j] = (float)r;
-      }
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        if constexpr (SYM) {
-          const TA *ar = reinterpret_cast<const TA *>(st + ((size_t)q * NT + tid) * (NA * sizeof(TA)));
-          aem1[q] = ar[OAE];
-          anm1[q] = ar[OAN];
-          atm1[q] = ar[OAT];
-        }
-        xm1[q] = x0[q];
-        x0[q] = xp1[q];
-      }
-    }
-    cp_async_wait<0>();
-    const double tot = block_sum(acc, s_red);
-    if (tid == 0) P.partials[tl.gtile] = tot;
     __syncthreads();
   }
 }

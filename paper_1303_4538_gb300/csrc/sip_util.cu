@@ -13,34 +13,20 @@ namespace sipk {
 const void *kernel_ptr(int kind, int Q, int R) {
   const void *p = kernel_ptr_64(kind, Q, R);
   if (!p) p = kernel_ptr_32(kind, Q, R);
-  if (!p) p = kernel_ptr_res(kind, Q, R);
   return p;
-}
-
-bool kernel_is_ticketed(int kind) {
-  return !(kind == K_RES64 || kind == K_RES64S || kind == K_RES32A || kind == K_RES32AS);
 }
 
 size_t kernel_smem(int kind, int Q, int R, int NT, int tab) {
   switch (kind) {
     case K_FACTOR:
     case K_FACTOR32: return fac_layout(Q, R, NT, tab).total;
-    case K_FWD64: return fwd_layout(8, false, false, Q, R, NT, tab).total;
-    case K_FWD64S: return fwd_layout(8, true, false, Q, R, NT, tab).total;
+    case K_FWD64: return fwd_layout(8, Q, R, NT, tab).total;
     case K_BWD64: return bwd_layout(8, false, false, Q, R, NT, tab).total;
-    case K_FWD32:
-    case K_FWD32N: return fwd_layout(4, false, false, Q, R, NT, tab).total;
-    case K_FWD32S:
-    case K_FWD32SN: return fwd_layout(4, true, false, Q, R, NT, tab).total;
-    case K_FWD32Z: return fwd_layout(4, false, true, Q, R, NT, tab).total;
+    case K_FWD32: return fwd_layout(4, Q, R, NT, tab).total;
     case K_BWD32: return bwd_layout(4, false, false, Q, R, NT, tab).total;
     case K_BWD32Z: return bwd_layout(4, true, false, Q, R, NT, tab).total;
     case K_BWD32U: return bwd_layout(4, false, true, Q, R, NT, tab).total;
     case K_BWD32ZU: return bwd_layout(4, true, true, Q, R, NT, tab).total;
-    case K_RES64: return res_layout(8, false, Q, R, NT, tab).total;
-    case K_RES64S: return res_layout(8, true, Q, R, NT, tab).total;
-    case K_RES32A: return res_layout(4, false, Q, R, NT, tab).total;
-    case K_RES32AS: return res_layout(4, true, Q, R, NT, tab).total;
     default: return 0;
   }
 }
@@ -127,7 +113,7 @@ cudaError_t launch_from_plan_f64(const double *src, double *dst, const DevBlock 
 
 struct Out7 { double *o[7]; };
 template <typename TF>
-__global__ void k_export(const TF *recF, const TF *recB, int rsf, Out7 O, DevBlock hb) {
+__global__ void k_export(const TF *recF, const TF *recB, Out7 O, DevBlock hb) {
   const long long n = (long long)hb.nx * hb.ny * hb.nz;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
@@ -135,7 +121,7 @@ __global__ void k_export(const TF *recF, const TF *recB, int rsf, Out7 O, DevBlo
     const int j = (int)((p / hb.nx) % hb.ny);
     const int k = (int)(p / ((long long)hb.nx * hb.ny));
     const long long a = plan_cell(hb, i, j, k);
-    const TF *f = recF + a * rsf;
+    const TF *f = recF + a * 4;
     const TF *b = recB + a * 4;
     O.o[0][p] = (double)f[REC_LB];
     O.o[1][p] = (double)f[REC_LW];
@@ -147,13 +133,13 @@ __global__ void k_export(const TF *recF, const TF *recB, int rsf, Out7 O, DevBlo
   }
 }
 
-cudaError_t launch_export_factors(const void *recF, const void *recB, int is_f32, int rsf, double *const out[7],
+cudaError_t launch_export_factors(const void *recF, const void *recB, int is_f32, double *const out[7],
                                   const DevBlock &hb, cudaStream_t st) {
   Out7 O;
   for (int q = 0; q < 7; ++q) O.o[q] = out[q];
   const int g = util_grid((long long)hb.nx * hb.ny * hb.nz);
-  if (is_f32) k_export<float><<<g, 256, 0, st>>>((const float *)recF, (const float *)recB, rsf, O, hb);
-  else k_export<double><<<g, 256, 0, st>>>((const double *)recF, (const double *)recB, rsf, O, hb);
+  if (is_f32) k_export<float><<<g, 256, 0, st>>>((const float *)recF, (const float *)recB, O, hb);
+  else k_export<double><<<g, 256, 0, st>>>((const double *)recF, (const double *)recB, O, hb);
   return cudaGetLastError();
 }
 
