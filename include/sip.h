@@ -112,6 +112,8 @@ typedef struct {
   int32_t graphs;          /* 1: queue iterations by replaying CUDA graphs captured on the
                               context's stream (one replay per 16 iterations; needs a
                               non-NULL stream, ignored while profiling); 0: launch by launch */
+  int32_t rows_per_thread; /* rows of a column tile each sweep thread walks (the tile is
+                              32 x rows_per_thread * warps): 0 (auto), 2 or 4 */
 } sip_options;
 
 /* Fills *opt with defaults: alpha 0.92, SIP_MODE_F64, inner_iters 4. Host pointer. */

@@ -481,44 +481,48 @@ std::vector<int> plan_kinds(int mode) {
   return {K_FACTOR32, K_FWD32, K_BWD32, K_BWD32Z, K_BWD32U, K_BWD32ZU};
 }
 
-// Tile shape: rows per thread Q and warps NW (tile = 32 x Q*NW).  Prefer the
-// shape whose tiles all fit on the GPU at once (one wave) and keep the most
-// SMs busy, then the fewest tile-to-tile hops; for every kernel the deepest
-// stage ring (6, else 4) that keeps the plan in one wave.
+// Tile shape: rows per thread Q and warps NW (tile = 32 x Q*NW), stage depth
+// R.  A sweep's time is (steps on its critical path) x (time of one step).
+// The critical path of a block walks the tile chain to its last tile, each
+// hop lagging by the tile's extent plus the start slack, then that tile's own
+// walk: (nTJ-1)(32 + lead) + (nTK-1)(TK + lead) + nx + 32 + TK - 2 steps.  A
+// step is latency-bound and grows with the warps resident on an SM (they
+// share the SM's load/store pipe): measured on GB300 (256^3 and 128^3
+// Poisson blocks, every shape) as 1 + beta x warps per SM with beta = 0.04
+// for the FP32 sweeps and 0.057 for FP64, and 1.45x longer with four rows per
+// thread than with two at the same TK.  Only shapes whose tiles are all
+// resident at once are taken (else the fewest waves); R = 4 unless forced
+// (a deeper ring measured slower: more start slack, more stale faces).
 struct ShapeChoice {
   int Q = 0, NW = 0, ntiles = 0;
   int R[K_NKINDS] = {}, cap[K_NKINDS] = {};
-  double score = -1e30;
+  double score = 1e300;
 };
 
 ShapeChoice choose_shape(sip_ctx *ctx, const std::vector<BlockHost> &blocks, const std::vector<int> &kinds,
-                         int tab_ints, int forceTK, int forceR) {
+                         int tab_ints, int forceTK, int forceR, int forceQ, bool fp64) {
+  const double beta = fp64 ? 0.057 : 0.04;
   ShapeChoice best;
   for (int Q : kQs)
     for (int NW = 1; NW <= 16; ++NW) {
       const int TK = Q * NW, NT = 32 * NW;
       if (forceTK > 0 && TK != forceTK) continue;
-      int ntiles = 0, hops = 0;
-      for (auto &bh : blocks) {
-        const int a = (bh.d.ny + kTJ - 1) / kTJ, b = (bh.d.nz + TK - 1) / TK;
-        ntiles += a * b;
-        hops = std::max(hops, a + b);
-      }
+      if (forceQ > 0 && Q != forceQ) continue;
+      if (forceQ == 0 && forceTK == 0 && Q != 2) continue;  // 2 rows per thread measured fastest
       ShapeChoice c;
       c.Q = Q;
       c.NW = NW;
-      c.ntiles = ntiles;
-      bool ok = true;
       int capmin = INT_MAX;
+      bool ok = true;
       for (int kind : kinds) {
         int bR = 0, bcap = 0;
-        for (int R : {6, 4}) {
+        for (int R : {4, 6}) {
           if (forceR > 0 && R != forceR) continue;
           const size_t smem = kernel_smem(kind, Q, R, NT, tab_ints);
           if (smem + ctx->kernel_static_smem > ctx->smem_optin) continue;
           const int capk = ctx->nsm * max_active(kernel_ptr(kind, Q, R), NT, smem);
-          if (capk >= ntiles) { bR = R; bcap = capk; break; }
           if (capk > bcap) { bR = R; bcap = capk; }
+          if (forceR == 0 && capk > 0 && R == 4) break;  // R = 4 when it fits
         }
         if (bcap < 1) { ok = false; break; }
         c.R[kind] = bR;
@@ -526,10 +530,20 @@ ShapeChoice choose_shape(sip_ctx *ctx, const std::vector<BlockHost> &blocks, con
         capmin = std::min(capmin, bcap);
       }
       if (!ok) continue;
-      const bool onewave = capmin >= ntiles;
-      const double cover = (double)std::min(ntiles, ctx->nsm) / ctx->nsm;
-      c.score = (onewave ? 10.0 : 0.0) + cover - 0.002 * hops - (Q == 4 ? 0.0005 : 0.0);
-      if (c.score > best.score) best = c;
+      long long steps = 0;
+      for (auto &bh : blocks) {
+        const int nTJ = (bh.d.ny + kTJ - 1) / kTJ, nTK = (bh.d.nz + TK - 1) / TK;
+        c.ntiles += nTJ * nTK;
+        const int R = c.R[kinds[1]];
+        const int lead = std::min(R + 1, std::max(bh.d.nx - 1, 0));
+        steps = std::max(steps, (long long)(nTJ - 1) * (kTJ + lead) + (long long)(nTK - 1) * (TK + lead) +
+                                    bh.d.nx + kTJ + TK - 2);
+      }
+      const int waves = (c.ntiles + capmin - 1) / capmin;
+      const double per_sm = (double)NW * std::max(1, (c.ntiles + ctx->nsm - 1) / ctx->nsm);
+      // four rows per thread: measured 1.45x the step time of two at equal TK
+      c.score = (double)steps * (1.0 + beta * per_sm) * (Q == 4 ? 1.45 : 1.0) * waves * (waves > 1 ? 4.0 : 1.0);
+      if (c.score < best.score) best = c;
     }
   return best;
 }
@@ -652,6 +666,8 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     return fail(ctx, SIP_ERR_INVALID_ARG, "tile_k must be 0 (auto) or an even number <= 64");
   if (opt.stages != 0 && opt.stages != 4 && opt.stages != 6)
     return fail(ctx, SIP_ERR_INVALID_ARG, "stages must be 0 (auto), 4 or 6");
+  if (opt.rows_per_thread != 0 && opt.rows_per_thread != 2 && opt.rows_per_thread != 4)
+    return fail(ctx, SIP_ERR_INVALID_ARG, "rows_per_thread must be 0 (auto), 2 or 4");
 
   sip_plan *p = new sip_plan();
   p->ctx = ctx;
@@ -670,7 +686,8 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     p->tab_ints = std::max(p->tab_ints, (int)(bh.PO.size() + bh.F.size()));
   }
   const std::vector<int> kinds = plan_kinds(p->mode);
-  const ShapeChoice sc = choose_shape(ctx, p->blocks, kinds, p->tab_ints, opt.tile_k, opt.stages);
+  const ShapeChoice sc = choose_shape(ctx, p->blocks, kinds, p->tab_ints, opt.tile_k, opt.stages, opt.rows_per_thread,
+                                      p->mode == SIP_MODE_F64);
   if (sc.Q == 0) {
     delete p;
     return fail(ctx, SIP_ERR_INVALID_ARG, "no tile shape fits on an SM");

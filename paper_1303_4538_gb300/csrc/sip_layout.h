@@ -4,7 +4,8 @@
 // Every sweep kernel's dynamic shared memory is
 //   [ PO + F tables of the current block ]
 //   [ R stages: per step the staged records of the thread's Q rows, then
-//     scalar slots (r; y and x; the FP64 iterate of the refinement) ]
+//     scalar slots (r; y and x; the FP64 iterate of the refinement), then the
+//     cells' block-local offsets (kept from the issue for the store) ]
 //   [ exchange between neighbouring warps, double buffered ]
 //   [ R stages of face records consumed by the tile's edge threads ]
 #pragma once
@@ -19,6 +20,7 @@ struct SweepLayout {
   size_t step;   // bytes of one stage
   size_t rec;    // bytes of the staged records inside a stage (Q * NT * rsb)
   size_t aux;    // bytes of an auxiliary 8-byte region after the records (x64)
+  size_t off;    // offset inside a stage of the cells' block-local offsets (Q * NT ints)
   size_t exch;   // bytes of the exchange area
   size_t faces;  // bytes of the face ring
   size_t total;
@@ -38,7 +40,8 @@ __host__ __device__ inline SweepLayout fwd_layout(int esize, int Q, int R, int N
   L.tab = lay_a16((size_t)tab_ints * 4);
   L.rec = (size_t)Q * NT * L.rsb;
   L.aux = 0;
-  L.step = lay_a16(L.rec + (size_t)L.nsv * NT * esize);
+  L.off = L.rec + (size_t)L.nsv * NT * esize;
+  L.step = lay_a16(L.off + (size_t)Q * NT * 4);
   L.exch = lay_a16((size_t)2 * NW * 32 * esize);
   L.faces = (size_t)R * L.fs * 2 * 8;
   L.total = L.tab + (size_t)R * L.step + L.exch + L.faces;
@@ -55,7 +58,8 @@ __host__ __device__ inline SweepLayout bwd_layout(int esize, bool zx, bool upd64
   L.tab = lay_a16((size_t)tab_ints * 4);
   L.rec = (size_t)Q * NT * L.rsb;
   L.aux = upd64 ? (size_t)Q * NT * 8 : 0;
-  L.step = lay_a16(L.rec + L.aux + (size_t)L.nsv * NT * esize);
+  L.off = L.rec + L.aux + (size_t)L.nsv * NT * esize;
+  L.step = lay_a16(L.off + (size_t)Q * NT * 4);
   L.exch = lay_a16((size_t)2 * NW * 32 * esize);
   L.faces = (size_t)R * L.fs * 2 * 8;
   L.total = L.tab + (size_t)R * L.step + L.exch + L.faces;

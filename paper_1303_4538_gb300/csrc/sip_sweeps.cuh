@@ -70,6 +70,19 @@ __device__ __forceinline__ void cp_async_wait() {
 __device__ __forceinline__ void st_relaxed_v2(uint64_t *p, uint64_t a, uint64_t b) {
   asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
 }
+// predicated forms (no branch in the caller): nothing happens when !pred
+__device__ __forceinline__ void st_relaxed_v2_if(uint64_t *p, uint64_t a, uint64_t b, bool pred) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %3, 0;\n @q st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};\n}\n" ::"l"(p),
+      "l"(a), "l"(b), "r"((int)pred)
+      : "memory");
+}
+__device__ __forceinline__ void cp_async_16_if(void *sdst, const void *gsrc, bool pred) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q cp.async.cg.shared.global [%0], [%1], 16;\n}\n" ::"r"(
+                   smem_u32(sdst)),
+               "l"(gsrc), "r"((int)pred)
+               : "memory");
+}
 __device__ __forceinline__ uint64_t ld_relaxed(const uint64_t *p) {
   uint64_t v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -111,6 +124,10 @@ struct Face<float> {
     const uint64_t tag = (uint64_t)ep << 32;
     st_relaxed_v2(p, tag | (uint64_t)__float_as_uint(v), tag);
   }
+  __device__ static void put_if(uint64_t *p, float v, unsigned ep, bool pred) {
+    const uint64_t tag = (uint64_t)ep << 32;
+    st_relaxed_v2_if(p, tag | (uint64_t)__float_as_uint(v), tag, pred);
+  }
   __device__ static float get(const uint64_t *w) { return __uint_as_float((unsigned)w[0]); }
 };
 template <>
@@ -119,6 +136,11 @@ struct Face<double> {
     const uint64_t tag = (uint64_t)ep << 32;
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     st_relaxed_v2(p, tag | (b & 0xffffffffull), tag | (b >> 32));
+  }
+  __device__ static void put_if(uint64_t *p, double v, unsigned ep, bool pred) {
+    const uint64_t tag = (uint64_t)ep << 32;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    st_relaxed_v2_if(p, tag | (b & 0xffffffffull), tag | (b >> 32), pred);
   }
   __device__ static double get(const uint64_t *w) {
     return __longlong_as_double((long long)((w[0] & 0xffffffffull) | (w[1] << 32)));
@@ -184,6 +206,25 @@ template <int W>
 __device__ __forceinline__ void rec_prefetch(uint64_t *sdst, const uint64_t *g) {
 #pragma unroll
   for (int q = 0; q < W; q += 2) cp_async_16_l2(sdst + q, g + q, true);
+}
+
+// The two words of a face record staged in shared memory (one 16-byte load).
+__device__ __forceinline__ void staged_words(const uint64_t *staged, uint64_t (&w)[2]) {
+  const ulonglong2 s2 = *reinterpret_cast<const ulonglong2 *>(staged);
+  w[0] = s2.x;
+  w[1] = s2.y;
+}
+
+// Row bases of a warp's Q rows for C = 32 / Q consecutive steps, one per
+// lane: lane l holds the base of row k0 + w Q + l % Q on local plane t of
+// step `first + l / Q` (0 where that plane row does not exist).  A step's
+// bases are then fetched with one shuffle per row.
+template <int Q>
+__device__ __forceinline__ int rowbase_chunk(const DevBlock &B, const int *sPO, const int *sF, int s0, int k,
+                                             int t, int nsteps) {
+  const int s = s0 + t, m = s - k;
+  const bool ok = t >= 0 && t < nsteps && k < B.nz && m >= 0 && m <= B.mmax;
+  return ok ? plane_row_base(sPO, sF, B.mmax, B.nx, s, k) : 0;
 }
 
 // Face storage of one tile: J face [nsteps_max][TK][W], then K face
@@ -485,12 +526,17 @@ __global__ void __launch_bounds__(512) k_factor(FacParams<TF> P) {
 // row-parallel kernel, so the wavefront carries only this recurrence.  r and y
 // may alias (in place): a cell's r is staged before its y is stored, and no
 // other cell reads it.
+//
+// Per step a thread issues the copies of step t + R - 1 (row bases from the
+// warp's row-base chunk, one shuffle per row; the cell offsets are kept in the
+// stage for the store) and computes step t from its stage.
 template <typename T, int Q, int R>
 __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_claim, s_blk;
   constexpr int W = 2;
-  constexpr int NCP = 4 * (int)sizeof(T) / 16;  // 16-byte copies per L record
+  constexpr int RBY = 4 * (int)sizeof(T);  // bytes of an L record
+  constexpr int C = 32 / Q;                // steps per row-base chunk
   const SweepCommon &c = P.c;
   const unsigned ep = sweep_prologue(c);
   if (threadIdx.x == 0) s_blk = -1;
@@ -515,37 +561,65 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
     load_tables(B, tl.blk, sPO, &s_blk);
     const int *sF = sPO + B.nplanes;
     const Geo<Q> g(B, tl);
-    const int NW = g.NW, lane = g.lane, w = g.w;
+    const int NW = g.NW, lane = g.lane, w = g.w, TK = g.TK;
     uint64_t *myf = tile_faces(c, B, tl.gtile);
-    uint64_t *upJ = g.hasS ? tile_faces(c, B, tl.gtile - 1) : nullptr;
-    uint64_t *upK = g.hasB ? tile_faces(c, B, tl.gtile - B.nTJ) : nullptr;
+    uint64_t *upJ = g.hasS ? tile_faces(c, B, tl.gtile - 1) : myf;
+    uint64_t *upK = g.hasB ? tile_faces(c, B, tl.gtile - B.nTJ) : myf;
     {
       const int lead = min(R + 1, B.nx - 1);
-      slack_gate<W>(upJ ? faceJ(upJ, B, lead + kTJ - 1, 0, W) : nullptr,
-                    upK ? faceK(upK, B, lead + g.TK - 1, 0, W) : nullptr, expect, c, abort, tr);
+      slack_gate<W>(g.hasS ? faceJ(upJ, B, lead + kTJ - 1, 0, W) : nullptr,
+                    g.hasB ? faceK(upK, B, lead + TK - 1, 0, W) : nullptr, expect, c, abort, tr);
     }
-    auto rb = [&](int s, int k) { return plane_row_base(sPO, sF, B.mmax, B.nx, s, k); };
+    // per-row invariants: cell of row q at local step t is i = t - tlo[q]
+    int tlo[Q];
+    bool colq[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      tlo[q] = lane + g.dk(q);
+      colq[q] = g.col(B, q);
+    }
+    const unsigned nxu = (unsigned)B.nx;
+    const long long kface = (long long)B.nsteps_max * TK * W;  // K faces follow the J faces
+    int chunk = 0, cb = -C;  // row-base chunk of issue steps [cb, cb + C)
+    const int kchunk = g.k0 + w * Q + lane % Q;
 
     auto issue = [&](int tt) {
       if (tt < g.nsteps) {
-        const int s = g.s0 + tt;
-        unsigned char *st = stage + (size_t)(tt % R) * L.step;
-        T *sc = reinterpret_cast<T *>(st + L.rec) + tid;
-        uint64_t *fs = fst + (size_t)(tt % R) * FS * W;
+        if (tt - cb >= C) {
+          cb += C;
+          chunk = rowbase_chunk<Q>(B, sPO, sF, g.s0, kchunk, cb + lane / Q, g.nsteps);
+        }
+        const int sl = tt % R;
+        unsigned char *st = stage + (size_t)sl * L.step;
+        T *sr = reinterpret_cast<T *>(st + L.rec) + tid;
+        int *so = reinterpret_cast<int *>(st + L.off) + tid;
+        uint64_t *fs = fst + (size_t)sl * FS * W;
+        // addresses of every row first, then the copies (the copies are
+        // ordered memory operations; keeping them together lets the
+        // address arithmetic of all rows overlap)
+        int off[Q];
+        bool v[Q];
+        long long a[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          const int i = g.i(tt, q);
-          const bool v = g.col(B, q) && i >= 0 && i < B.nx;
-          const long long a = v ? B.cell0 + rb(s, g.k(q)) + g.j : 0;
-          unsigned char *d = st + ((size_t)q * NT + tid) * (4 * sizeof(T));
-          const unsigned char *src = reinterpret_cast<const unsigned char *>(P.rec + a * 4);
-#pragma unroll
-          for (int z = 0; z < NCP; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v);
-          cp_async_zfill<sizeof(T)>(sc + q * NT, P.r + a, v);
-          if (lane == 0 && g.hasS && v) rec_prefetch<W>(fs + g.dk(q) * W, faceJ(upJ, B, tt + kTJ - 1, g.dk(q), W));
-          if (q == 0 && g.eB && g.hasB && v)
-            rec_prefetch<W>(fs + (g.TK + lane) * W, faceK(upK, B, tt + g.TK - 1, lane, W));
+          off[q] = __shfl_sync(0xffffffffu, chunk, (tt - cb) * Q + q) + g.j;
+          v[q] = colq[q] && (unsigned)(tt - tlo[q]) < nxu;
+          a[q] = v[q] ? B.cell0 + off[q] : 0;
         }
+        const uint64_t *fj = upJ + ((long long)(tt + kTJ - 1) * TK + w * Q) * W;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          unsigned char *d = st + ((size_t)q * NT + tid) * RBY;
+          const unsigned char *src = reinterpret_cast<const unsigned char *>(P.rec + a[q] * 4);
+#pragma unroll
+          for (int z = 0; z < RBY / 16; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v[q]);
+          cp_async_zfill<sizeof(T)>(sr + q * NT, P.r + a[q], v[q]);
+          so[q * NT] = off[q];
+          cp_async_16_if(fs + g.dk(q) * W, fj + q * W, lane == 0 && g.hasS && v[q]);
+        }
+        if (g.eB)  // warp-uniform
+          cp_async_16_if(fs + (TK + lane) * W, upK + kface + ((long long)(tt + TK - 1) * kTJ + lane) * W,
+                         g.hasB && v[0]);
       }
       cp_async_commit();
     };
@@ -558,37 +632,47 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
     for (int t = 0; t < g.nsteps; ++t) {
       issue(t + R - 1);
       cp_async_wait<R - 1>();
-      const unsigned char *st = stage + (size_t)(t % R) * L.step;
-      const T *sc = reinterpret_cast<const T *>(st + L.rec) + tid;
-      const uint64_t *fs = fst + (size_t)(t % R) * FS * W;
+      const int sl = t % R;
+      const unsigned char *st = stage + (size_t)sl * L.step;
+      const T *sr = reinterpret_cast<const T *>(st + L.rec) + tid;
+      const int *so = reinterpret_cast<const int *>(st + L.off) + tid;
+      const uint64_t *fs = fst + (size_t)sl * FS * W;
       T *E = exB + (size_t)(t & 1) * NW * 32;
       E[w * 32 + lane] = ym1[Q - 1];
-      T yK = T(0);
-      if (g.eB) {
-        const int i0 = g.i(t, 0);
-        if (g.hasB && g.col(B, 0) && i0 >= 0 && i0 < B.nx) {
-          uint64_t wv[W];
-          rec_take<W>(fs + (g.TK + lane) * W, faceK(upK, B, t + g.TK - 1, lane, W), expect, wv, c, abort, tr);
-          yK = Face<T>::get(wv);
-        }
-      }
       __syncthreads();
+      // faces of this step: J (lane 0, per row) and K (warp 0, row 0); a stale
+      // staged copy is re-read from L2 (rare: one warp-uniform branch)
+      bool act[Q], needJ[Q];
+      uint64_t jw[Q][2], kw[2] = {0, 0};
+      bool stale = false;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        act[q] = colq[q] && (unsigned)(t - tlo[q]) < nxu;
+        needJ[q] = lane == 0 && g.hasS && act[q];
+        staged_words(fs + g.dk(q) * W, jw[q]);
+        stale |= needJ[q] && !rec_ok<2>(jw[q], expect);
+      }
+      const bool needK = g.eB && g.hasB && act[0];
+      if (g.eB) {
+        staged_words(fs + (TK + lane) * W, kw);
+        stale |= needK && !rec_ok<2>(kw, expect);
+      }
+      if (__any_sync(0xffffffffu, stale)) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+          if (needJ[q] && !rec_ok<2>(jw[q], expect))
+            face_wait<2>(upJ + ((long long)(t + kTJ - 1) * TK + g.dk(q)) * W, expect, jw[q], c, abort, tr);
+        if (needK && !rec_ok<2>(kw, expect))
+          face_wait<2>(upK + kface + ((long long)(t + TK - 1) * kTJ + lane) * W, expect, kw, c, abort, tr);
+      }
+      const T yK = needK ? Face<T>::get(kw) : T(0);
       T ny[Q];
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        const int i = g.i(t, q);
-        const bool act = g.col(B, q) && i >= 0 && i < B.nx;
-        const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * (4 * sizeof(T)));
-        const T r = sc[q * NT];
+        const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * RBY);
+        const T r = sr[q * NT];
         T yS = shfl_up1(ym1[q]);
-        if (lane == 0) {
-          yS = T(0);
-          if (g.hasS && act) {
-            uint64_t wv[W];
-            rec_take<W>(fs + g.dk(q) * W, faceJ(upJ, B, t + kTJ - 1, g.dk(q), W), expect, wv, c, abort, tr);
-            yS = Face<T>::get(wv);
-          }
-        }
+        if (lane == 0) yS = needJ[q] ? Face<T>::get(jw[q]) : T(0);
         T yB;
         if (q > 0) yB = ym1[q > 0 ? q - 1 : 0];
         else if (w > 0) yB = E[(w - 1) * 32 + lane];
@@ -596,15 +680,17 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
         T y = fma(-rec[REC_LB], yB, r);
         y = fma(-rec[REC_LW], ym1[q], y);
         y = fma(-rec[REC_LS], yS, y);
-        y = y * rec[REC_RLP];
-        if (act) {
-          const long long a = B.cell0 + rb(g.s0 + t, g.k(q)) + g.j;
-          P.y[a] = y;
-          if (lane == kTJ - 1 && g.hasN) Face<T>::put(faceJ(myf, B, t, g.dk(q), W), y, ep);
-          if (q == Q - 1 && g.eT && g.hasT) Face<T>::put(faceK(myf, B, t, lane, W), y, ep);
-        }
-        ny[q] = act ? y : T(0);
+        ny[q] = act[q] ? y * rec[REC_RLP] : T(0);
       }
+      // stores last: y, then the face records (ordered memory operations)
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        if (act[q]) P.y[B.cell0 + so[q * NT]] = ny[q];
+      uint64_t *pj = myf + ((long long)t * TK + w * Q) * W;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) Face<T>::put_if(pj + q * W, ny[q], ep, lane == kTJ - 1 && g.hasN && act[q]);
+      if (g.eT)  // warp-uniform
+        Face<T>::put_if(myf + kface + ((long long)t * kTJ + lane) * W, ny[Q - 1], ep, g.hasT && act[Q - 1]);
 #pragma unroll
       for (int q = 0; q < Q; ++q) ym1[q] = ny[q];
     }
@@ -618,12 +704,14 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
 // backward3d with the update: d_P = y_P - UE d_E - UN d_N - UT d_T
 // (descending planes), x_P <- x_P + d_P.  ZX: x = 0 on entry (x_P <- d_P).
 // UPD64 (refined mode, last inner iteration): x64_P += (double) x_P instead
-// of storing x_P.
+// of storing x_P.  Backward step u processes local plane t = last - u.
 template <typename T, bool ZX, bool UPD64, int Q, int R>
 __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_claim, s_blk;
   constexpr int W = 2;
+  constexpr int RBY = 4 * (int)sizeof(T);  // bytes of a U record
+  constexpr int C = 32 / Q;
   constexpr int SY = 0, SX = Q;  // scalar slots
   const SweepCommon &c = P.c;
   const unsigned ep = sweep_prologue(c);
@@ -635,7 +723,7 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
   const SweepLayout L = bwd_layout((int)sizeof(T), ZX, UPD64, Q, R, NT, c.tab_ints);
   int *sPO = reinterpret_cast<int *>(smem_raw);
   unsigned char *stage = smem_raw + L.tab;
-  T *exT = reinterpret_cast<T *>(stage + (size_t)R * L.step);  // [2][NW][32]: row 0 of each warp
+  T *exT = reinterpret_cast<T *>(stage + (size_t)R * L.step);  // [2][NW][32]: d of a warp's first row
   uint64_t *fst = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(exT) + L.exch);
   const int FS = L.fs;
   bool abort = false;
@@ -649,47 +737,69 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
     load_tables(B, tl.blk, sPO, &s_blk);
     const int *sF = sPO + B.nplanes;
     const Geo<Q> g(B, tl);
-    const int NW = g.NW, lane = g.lane, w = g.w;
+    const int NW = g.NW, lane = g.lane, w = g.w, TK = g.TK;
     uint64_t *myf = tile_faces(c, B, tl.gtile);
-    uint64_t *dnJ = g.hasN ? tile_faces(c, B, tl.gtile + 1) : nullptr;
-    uint64_t *dnK = g.hasT ? tile_faces(c, B, tl.gtile + B.nTJ) : nullptr;
+    uint64_t *dnJ = g.hasN ? tile_faces(c, B, tl.gtile + 1) : myf;
+    uint64_t *dnK = g.hasT ? tile_faces(c, B, tl.gtile + B.nTJ) : myf;
     const int last = g.nsteps - 1;
     {
       // the consumer of the last valid row (column) needs, `lead` steps into
       // the walk, cell i = nx-1-lead, published on the producer's step i + lane
       const int lead = min(R + 1, B.nx - 1);
       const int i = B.nx - 1 - lead;
-      slack_gate<W>(dnJ ? faceJ(dnJ, B, i + g.nkt - 1, g.nkt - 1, W) : nullptr,
-                    dnK ? faceK(dnK, B, i + g.njt - 1, g.njt - 1, W) : nullptr, expect, c, abort, tr);
+      slack_gate<W>(g.hasN ? faceJ(dnJ, B, i + g.nkt - 1, g.nkt - 1, W) : nullptr,
+                    g.hasT ? faceK(dnK, B, i + g.njt - 1, g.njt - 1, W) : nullptr, expect, c, abort, tr);
     }
-    auto rb = [&](int s, int k) { return plane_row_base(sPO, sF, B.mmax, B.nx, s, k); };
+    int tlo[Q];
+    bool colq[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      tlo[q] = lane + g.dk(q);
+      colq[q] = g.col(B, q);
+    }
+    const unsigned nxu = (unsigned)B.nx;
+    const long long kface = (long long)B.nsteps_max * TK * W;
+    int chunk = 0, cb = -C;  // row-base chunk of issue steps [cb, cb + C)
+    const int kchunk = g.k0 + w * Q + lane % Q;
 
-    // backward step u processes local plane t = last - u
     auto issue = [&](int uu) {
       if (uu < g.nsteps) {
+        if (uu - cb >= C) {
+          cb += C;
+          chunk = rowbase_chunk<Q>(B, sPO, sF, g.s0, kchunk, last - (cb + lane / Q), g.nsteps);
+        }
         const int t = last - uu;
-        const int s = g.s0 + t;
-        unsigned char *st = stage + (size_t)(uu % R) * L.step;
+        const int sl = uu % R;
+        unsigned char *st = stage + (size_t)sl * L.step;
         double *s64 = reinterpret_cast<double *>(st + L.rec) + tid;
         T *sc = reinterpret_cast<T *>(st + L.rec + L.aux) + tid;
-        uint64_t *fs = fst + (size_t)(uu % R) * FS * W;
+        int *so = reinterpret_cast<int *>(st + L.off) + tid;
+        uint64_t *fs = fst + (size_t)sl * FS * W;
+        int off[Q];
+        bool v[Q];
+        long long a[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          const int i = g.i(t, q);
-          const bool v = g.col(B, q) && i >= 0 && i < B.nx;
-          const long long a = v ? B.cell0 + rb(s, g.k(q)) + g.j : 0;
-          unsigned char *d = st + ((size_t)q * NT + tid) * (4 * sizeof(T));
-          const unsigned char *src = reinterpret_cast<const unsigned char *>(P.rec + a * 4);
-#pragma unroll
-          for (int z = 0; z < (int)sizeof(T) / 4; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v);
-          cp_async_zfill<sizeof(T)>(sc + (SY + q) * NT, P.y + a, v);
-          if constexpr (!ZX) cp_async_zfill<sizeof(T)>(sc + (SX + q) * NT, P.x + a, v);
-          if constexpr (UPD64) cp_async_zfill<8>(s64 + (size_t)q * NT, P.x64 + a, v);
-          if (lane == kTJ - 1 && g.hasN && v)
-            rec_prefetch<W>(fs + g.dk(q) * W, faceJ(dnJ, B, t - (kTJ - 1), g.dk(q), W));
-          if (q == Q - 1 && g.eT && g.hasT && v)
-            rec_prefetch<W>(fs + (g.TK + lane) * W, faceK(dnK, B, t - (g.TK - 1), lane, W));
+          off[q] = __shfl_sync(0xffffffffu, chunk, (uu - cb) * Q + q) + g.j;
+          v[q] = colq[q] && (unsigned)(t - tlo[q]) < nxu;
+          a[q] = v[q] ? B.cell0 + off[q] : 0;
         }
+        const uint64_t *fj = dnJ + ((long long)(t - (kTJ - 1)) * TK + w * Q) * W;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          unsigned char *d = st + ((size_t)q * NT + tid) * RBY;
+          const unsigned char *src = reinterpret_cast<const unsigned char *>(P.rec + a[q] * 4);
+#pragma unroll
+          for (int z = 0; z < RBY / 16; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v[q]);
+          cp_async_zfill<sizeof(T)>(sc + (SY + q) * NT, P.y + a[q], v[q]);
+          if constexpr (!ZX) cp_async_zfill<sizeof(T)>(sc + (SX + q) * NT, P.x + a[q], v[q]);
+          if constexpr (UPD64) cp_async_zfill<8>(s64 + (size_t)q * NT, P.x64 + a[q], v[q]);
+          so[q * NT] = off[q];
+          cp_async_16_if(fs + g.dk(q) * W, fj + q * W, lane == kTJ - 1 && g.hasN && v[q]);
+        }
+        if (g.eT)  // warp-uniform
+          cp_async_16_if(fs + (TK + lane) * W, dnK + kface + ((long long)(t - (TK - 1)) * kTJ + lane) * W,
+                         g.hasT && v[Q - 1]);
       }
       cp_async_commit();
     };
@@ -702,59 +812,74 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
     for (int u = 0; u < g.nsteps; ++u) {
       issue(u + R - 1);
       cp_async_wait<R - 1>();
-      const unsigned char *st = stage + (size_t)(u % R) * L.step;
+      const int sl = u % R;
+      const unsigned char *st = stage + (size_t)sl * L.step;
       const double *s64 = reinterpret_cast<const double *>(st + L.rec) + tid;
       const T *sc = reinterpret_cast<const T *>(st + L.rec + L.aux) + tid;
-      const uint64_t *fs = fst + (size_t)(u % R) * FS * W;
+      const int *so = reinterpret_cast<const int *>(st + L.off) + tid;
+      const uint64_t *fs = fst + (size_t)sl * FS * W;
       const int t = last - u;
-      const int buf = u & 1;
-      exT[((size_t)buf * NW + w) * 32 + lane] = dE[0];
-      T dK = T(0);
-      if (g.eT) {
-        const int iq = g.i(t, Q - 1);
-        if (g.hasT && g.col(B, Q - 1) && iq >= 0 && iq < B.nx) {
-          uint64_t wv[W];
-          rec_take<W>(fs + (g.TK + lane) * W, faceK(dnK, B, t - (g.TK - 1), lane, W), expect, wv, c, abort, tr);
-          dK = Face<T>::get(wv);
-        }
-      }
+      T *E = exT + (size_t)(u & 1) * NW * 32;
+      E[w * 32 + lane] = dE[0];
       __syncthreads();
-      T nd[Q];
+      // faces of this step: J (lane 31, per row) and K (last warp, last row)
+      bool act[Q], needJ[Q];
+      uint64_t jw[Q][2], kw[2] = {0, 0};
+      bool stale = false;
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        const int i = g.i(t, q);
-        const bool act = g.col(B, q) && i >= 0 && i < B.nx;
-        const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * (4 * sizeof(T)));
+        act[q] = colq[q] && (unsigned)(t - tlo[q]) < nxu;
+        needJ[q] = lane == kTJ - 1 && g.hasN && act[q];
+        staged_words(fs + g.dk(q) * W, jw[q]);
+        stale |= needJ[q] && !rec_ok<2>(jw[q], expect);
+      }
+      const bool needK = g.eT && g.hasT && act[Q - 1];
+      if (g.eT) {
+        staged_words(fs + (TK + lane) * W, kw);
+        stale |= needK && !rec_ok<2>(kw, expect);
+      }
+      if (__any_sync(0xffffffffu, stale)) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+          if (needJ[q] && !rec_ok<2>(jw[q], expect))
+            face_wait<2>(dnJ + ((long long)(t - (kTJ - 1)) * TK + g.dk(q)) * W, expect, jw[q], c, abort, tr);
+        if (needK && !rec_ok<2>(kw, expect))
+          face_wait<2>(dnK + kface + ((long long)(t - (TK - 1)) * kTJ + lane) * W, expect, kw, c, abort, tr);
+      }
+      const T dK = needK ? Face<T>::get(kw) : T(0);
+      T nd[Q], xv[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * RBY);
         T dN = shfl_dn1(dE[q]);
-        if (lane == kTJ - 1) {
-          dN = T(0);
-          if (g.hasN && act) {
-            uint64_t wv[W];
-            rec_take<W>(fs + g.dk(q) * W, faceJ(dnJ, B, t - (kTJ - 1), g.dk(q), W), expect, wv, c, abort, tr);
-            dN = Face<T>::get(wv);
-          }
-        }
+        if (lane == kTJ - 1) dN = needJ[q] ? Face<T>::get(jw[q]) : T(0);
         T dT;
         if (q < Q - 1) dT = dE[q < Q - 1 ? q + 1 : 0];
-        else if (w < NW - 1) dT = exT[((size_t)buf * NW + w + 1) * 32 + lane];
+        else if (w < NW - 1) dT = E[(w + 1) * 32 + lane];
         else dT = dK;
         T d = fma(-rec[RECB_UE], dE[q], sc[(SY + q) * NT]);
         d = fma(-rec[RECB_UN], dN, d);
         d = fma(-rec[RECB_UT], dT, d);
-        if (act) {
-          const long long a = B.cell0 + rb(g.s0 + t, g.k(q)) + g.j;
-          T xn = d;
-          if constexpr (!ZX) xn = sc[(SX + q) * NT] + d;
-          if constexpr (UPD64) {
-            P.x64[a] = s64[(size_t)q * NT] + (double)xn;
-          } else {
-            P.x[a] = xn;
-          }
-          if (lane == 0 && g.hasS) Face<T>::put(faceJ(myf, B, t, g.dk(q), W), d, ep);
-          if (q == 0 && g.eB && g.hasB) Face<T>::put(faceK(myf, B, t, lane, W), d, ep);
-        }
-        nd[q] = act ? d : T(0);
+        T xn = d;
+        if constexpr (!ZX) xn = sc[(SX + q) * NT] + d;
+        xv[q] = xn;
+        nd[q] = act[q] ? d : T(0);
       }
+      // stores last: the update, then the face records (ordered memory operations)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const long long a = B.cell0 + so[q * NT];
+        if constexpr (UPD64) {
+          if (act[q]) P.x64[a] = s64[(size_t)q * NT] + (double)xv[q];
+        } else {
+          if (act[q]) P.x[a] = xv[q];
+        }
+      }
+      uint64_t *pj = myf + ((long long)t * TK + w * Q) * W;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) Face<T>::put_if(pj + q * W, nd[q], ep, lane == 0 && g.hasS && act[q]);
+      if (g.eB)  // warp-uniform
+        Face<T>::put_if(myf + kface + ((long long)t * kTJ + lane) * W, nd[0], ep, g.hasB && act[0]);
 #pragma unroll
       for (int q = 0; q < Q; ++q) dE[q] = nd[q];
     }

@@ -69,6 +69,7 @@ class sip_options(ctypes.Structure):
         ("alpha", ctypes.c_double), ("mode", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
         ("max_spin", ctypes.c_int64), ("tile_j", ctypes.c_int32), ("tile_k", ctypes.c_int32),
         ("stages", ctypes.c_int32), ("debug_stall", ctypes.c_int32), ("graphs", ctypes.c_int32),
+        ("rows_per_thread", ctypes.c_int32),
     ]
 
 

@@ -42,7 +42,9 @@ class GpuSystem:
         opts = sip.default_options(alpha=alpha, mode=mode, inner_iters=inner, max_spin=max_spin,
                                    debug_stall=stall, graphs=graphs)
         if tile:
-            opts.tile_j, opts.tile_k = tile
+            opts.tile_j, opts.tile_k = tile[:2]
+            if len(tile) > 2:
+                opts.rows_per_thread = tile[2]
         torch.cuda.synchronize()
         ifs = None
         if ifaces:

@@ -55,8 +55,11 @@ def test_iterations_match_oracle(shape, kind):
     g.close()
 
 
-@pytest.mark.parametrize("tile", [(32, 2), (32, 4), (32, 6), (32, 8), (32, 12)])
+@pytest.mark.parametrize("tile", [(32, 2), (32, 4), (32, 6), (32, 8), (32, 12), (32, 8, 2), (32, 8, 4),
+                                  (32, 16, 4), (32, 20, 4)])
 def test_tile_shapes_agree(tile):
+    """(tile_j, tile_k[, rows_per_thread]): every column-tile shape gives the
+    oracle's iterates."""
     shape = (23, 45, 37)
     blk = W.make_block(*shape, seed=31, kind="convdiff")
     g = GpuSystem(blk, tile=tile)
@@ -238,4 +241,8 @@ def test_invalid_arguments():
     d = sip.make_desc(2, 2, 2, [z] * 7, z, z)
     with pytest.raises(sip.SipError):
         sip.Plan(ctx, [d], sip.default_options(alpha=1.5))
+    for bad in (dict(rows_per_thread=3), dict(stages=5), dict(tile_k=7), dict(tile_j=16)):
+        with pytest.raises(sip.SipError) as e:
+            sip.Plan(ctx, [d], sip.default_options(**bad))
+        assert e.value.code == sip.SIP_ERR_INVALID_ARG
     ctx.close()
