@@ -515,9 +515,13 @@ ShapeChoice choose_shape(sip_ctx *ctx, const std::vector<BlockHost> &blocks, con
       int capmin = INT_MAX;
       bool ok = true;
       for (int kind : kinds) {
+        const bool fac = kind == K_FACTOR || kind == K_FACTOR32;
         int bR = 0, bcap = 0;
-        for (int R : {4, 6}) {
-          if (forceR > 0 && R != forceR) continue;
+        for (int R : {4, 6, 2}) {
+          // the one-off factorisation may drop to a 2-stage ring when its
+          // 64-byte input records do not fit a wide tile
+          if (R == 2 ? !fac : (forceR > 0 && R != forceR)) continue;
+          if (R == 2 && bcap > 0) break;
           const size_t smem = kernel_smem(kind, Q, R, NT, tab_ints);
           if (smem + ctx->kernel_static_smem > ctx->smem_optin) continue;
           const int capk = ctx->nsm * max_active(kernel_ptr(kind, Q, R), NT, smem);

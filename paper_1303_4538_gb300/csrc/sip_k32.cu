@@ -8,6 +8,7 @@ namespace sipk {
 
 template <int Q, int R>
 static const void *pick32(int kind) {
+  if constexpr (R == 2) return kind == K_FACTOR32 ? (const void *)k_factor<float, Q, R> : nullptr;
   switch (kind) {
     case K_FACTOR32: return (const void *)k_factor<float, Q, R>;
     case K_FWD32: return (const void *)k_forward<float, Q, R>;
@@ -20,8 +21,8 @@ static const void *pick32(int kind) {
 }
 
 const void *kernel_ptr_32(int kind, int Q, int R) {
-  if (Q == 2) return R == 4 ? pick32<2, 4>(kind) : R == 6 ? pick32<2, 6>(kind) : nullptr;
-  if (Q == 4) return R == 4 ? pick32<4, 4>(kind) : R == 6 ? pick32<4, 6>(kind) : nullptr;
+  if (Q == 2) return R == 2 ? pick32<2, 2>(kind) : R == 4 ? pick32<2, 4>(kind) : R == 6 ? pick32<2, 6>(kind) : nullptr;
+  if (Q == 4) return R == 2 ? pick32<4, 2>(kind) : R == 4 ? pick32<4, 4>(kind) : R == 6 ? pick32<4, 6>(kind) : nullptr;
   return nullptr;
 }
 

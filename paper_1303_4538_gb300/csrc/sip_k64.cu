@@ -7,6 +7,7 @@ namespace sipk {
 
 template <int Q, int R>
 static const void *pick64(int kind) {
+  if constexpr (R == 2) return kind == K_FACTOR ? (const void *)k_factor<double, Q, R> : nullptr;
   switch (kind) {
     case K_FACTOR: return (const void *)k_factor<double, Q, R>;
     case K_FWD64: return (const void *)k_forward<double, Q, R>;
@@ -16,8 +17,8 @@ static const void *pick64(int kind) {
 }
 
 const void *kernel_ptr_64(int kind, int Q, int R) {
-  if (Q == 2) return R == 4 ? pick64<2, 4>(kind) : R == 6 ? pick64<2, 6>(kind) : nullptr;
-  if (Q == 4) return R == 4 ? pick64<4, 4>(kind) : R == 6 ? pick64<4, 6>(kind) : nullptr;
+  if (Q == 2) return R == 2 ? pick64<2, 2>(kind) : R == 4 ? pick64<2, 4>(kind) : R == 6 ? pick64<2, 6>(kind) : nullptr;
+  if (Q == 4) return R == 2 ? pick64<4, 2>(kind) : R == 4 ? pick64<4, 4>(kind) : R == 6 ? pick64<4, 6>(kind) : nullptr;
   return nullptr;
 }
 

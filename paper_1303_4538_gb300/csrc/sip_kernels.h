@@ -27,7 +27,7 @@ enum KernelKind {
 constexpr bool kind_is_row(int kind) { return kind >= K_RES64 && kind < K_NKINDS; }
 
 constexpr int kQs[2] = {2, 4};
-constexpr int kRs[2] = {4, 6};
+constexpr int kRs[3] = {2, 4, 6};  // 2: the factorisation only (wide tiles)
 
 // sweep kernel of a kind (nullptr for the row kinds)
 const void *kernel_ptr(int kind, int Q, int R);
