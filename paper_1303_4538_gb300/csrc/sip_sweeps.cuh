@@ -128,6 +128,12 @@ struct Face<float> {
     const uint64_t tag = (uint64_t)ep << 32;
     st_relaxed_v2_if(p, tag | (uint64_t)__float_as_uint(v), tag, pred);
   }
+  // two values in one record (one per word): the J faces of a thread's row pair
+  __device__ static void put2_if(uint64_t *p, float a, float b, unsigned ep, bool pred) {
+    const uint64_t tag = (uint64_t)ep << 32;
+    st_relaxed_v2_if(p, tag | (uint64_t)__float_as_uint(a), tag | (uint64_t)__float_as_uint(b), pred);
+  }
+  __device__ static float get_hi(const uint64_t *w) { return __uint_as_float((unsigned)w[1]); }
   __device__ static float get(const uint64_t *w) { return __uint_as_float((unsigned)w[0]); }
 };
 template <>
@@ -519,6 +525,23 @@ __global__ void __launch_bounds__(512) k_factor(FacParams<TF> P) {
   }
 }
 
+// J face records carry one row's value, or in FP32 a row pair's (one value
+// per 8-byte word), so a warp moves Q/2 records per step instead of Q.
+template <typename T, int Q>
+__host__ __device__ constexpr int face_pair() {
+  return (sizeof(T) == 4 && Q % 2 == 0) ? 2 : 1;
+}
+template <typename T, int PJ>
+__device__ __forceinline__ T face_row(const uint64_t (&w)[2], int q) {
+  if constexpr (PJ == 2) return (q & 1) ? Face<T>::get_hi(w) : Face<T>::get(w);
+  else return Face<T>::get(w);
+}
+template <typename T, int PJ, int Q>
+__device__ __forceinline__ void face_put(uint64_t *p, const T (&v)[Q], int q, unsigned ep, bool pred) {
+  if constexpr (PJ == 2) Face<T>::put2_if(p, v[q], v[q + 1], ep, pred);
+  else Face<T>::put_if(p, v[q], ep, pred);
+}
+
 // ============================================================ forward sweep
 // The substitution half of resforward3d: y = L^{-1} r with
 //   y_P = (r_P - LB y_B - LW y_W - LS y_S) * (1/LP),  ascending planes.
@@ -537,6 +560,7 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
   constexpr int W = 2;
   constexpr int RBY = 4 * (int)sizeof(T);  // bytes of an L record
   constexpr int C = 32 / Q;                // steps per row-base chunk
+  constexpr int PJ = face_pair<T, Q>();    // rows per J face record
   const SweepCommon &c = P.c;
   const unsigned ep = sweep_prologue(c);
   if (threadIdx.x == 0) s_blk = -1;
@@ -582,6 +606,16 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
     const long long kface = (long long)B.nsteps_max * TK * W;  // K faces follow the J faces
     int chunk = 0, cb = -C;  // row-base chunk of issue steps [cb, cb + C)
     const int kchunk = g.k0 + w * Q + lane % Q;
+    // the block's arrays (cell offsets inside a block fit in 32 bits)
+    const T *recb = P.rec + B.cell0 * 4;
+    const T *rb = P.r + B.cell0;
+    T *yb = P.y + B.cell0;
+    // running face pointers: records read by the copies of issue step tt and
+    // written at compute step t (row slot w Q; K slot lane)
+    const uint64_t *fjn = upJ + ((long long)(kTJ - 1) * TK + w * Q) * W;
+    const uint64_t *fkn = upK + kface + ((long long)(TK - 1) * kTJ + lane) * W;
+    uint64_t *pjn = myf + (long long)w * Q * W;
+    uint64_t *pkn = myf + kface + (long long)lane * W;
 
     auto issue = [&](int tt) {
       if (tt < g.nsteps) {
@@ -599,27 +633,30 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
         // address arithmetic of all rows overlap)
         int off[Q];
         bool v[Q];
-        long long a[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           off[q] = __shfl_sync(0xffffffffu, chunk, (tt - cb) * Q + q) + g.j;
           v[q] = colq[q] && (unsigned)(tt - tlo[q]) < nxu;
-          a[q] = v[q] ? B.cell0 + off[q] : 0;
         }
-        const uint64_t *fj = upJ + ((long long)(tt + kTJ - 1) * TK + w * Q) * W;
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
+          const int o = v[q] ? off[q] : 0;
           unsigned char *d = st + ((size_t)q * NT + tid) * RBY;
-          const unsigned char *src = reinterpret_cast<const unsigned char *>(P.rec + a[q] * 4);
+          const unsigned char *src = reinterpret_cast<const unsigned char *>(recb + o * 4);
 #pragma unroll
           for (int z = 0; z < RBY / 16; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v[q]);
-          cp_async_zfill<sizeof(T)>(sr + q * NT, P.r + a[q], v[q]);
+          cp_async_zfill<sizeof(T)>(sr + q * NT, rb + o, v[q]);
           so[q * NT] = off[q];
-          cp_async_16_if(fs + g.dk(q) * W, fj + q * W, lane == 0 && g.hasS && v[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < Q; q += PJ) {
+          const bool vq = PJ == 2 ? (v[q] || v[q + PJ - 1]) : v[q];
+          cp_async_16_if(fs + (w * Q + q) * W, fjn + q * W, lane == 0 && g.hasS && vq);
         }
         if (g.eB)  // warp-uniform
-          cp_async_16_if(fs + (TK + lane) * W, upK + kface + ((long long)(tt + TK - 1) * kTJ + lane) * W,
-                         g.hasB && v[0]);
+          cp_async_16_if(fs + (TK + lane) * W, fkn, g.hasB && v[0]);
+        fjn += (long long)TK * W;
+        fkn += (long long)kTJ * W;
       }
       cp_async_commit();
     };
@@ -640,17 +677,22 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
       T *E = exB + (size_t)(t & 1) * NW * 32;
       E[w * 32 + lane] = ym1[Q - 1];
       __syncthreads();
-      // faces of this step: J (lane 0, per row) and K (warp 0, row 0); a stale
-      // staged copy is re-read from L2 (rare: one warp-uniform branch)
-      bool act[Q], needJ[Q];
-      uint64_t jw[Q][2], kw[2] = {0, 0};
+      // faces of this step: J (lane 0, one record per row, or per row pair
+      // in FP32) and K (warp 0, row 0); a stale staged copy is re-read from
+      // L2 (rare: one warp-uniform branch)
+      bool act[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) act[q] = colq[q] && (unsigned)(t - tlo[q]) < nxu;
+      constexpr int NJ = Q / PJ;
+      bool needJ[NJ];
+      uint64_t jw[NJ][2], kw[2] = {0, 0};
       bool stale = false;
 #pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        act[q] = colq[q] && (unsigned)(t - tlo[q]) < nxu;
-        needJ[q] = lane == 0 && g.hasS && act[q];
-        staged_words(fs + g.dk(q) * W, jw[q]);
-        stale |= needJ[q] && !rec_ok<2>(jw[q], expect);
+      for (int r = 0; r < NJ; ++r) {
+        const int q = r * PJ;
+        needJ[r] = lane == 0 && g.hasS && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]);
+        staged_words(fs + (w * Q + q) * W, jw[r]);
+        stale |= needJ[r] && !rec_ok<2>(jw[r], expect);
       }
       const bool needK = g.eB && g.hasB && act[0];
       if (g.eB) {
@@ -659,9 +701,9 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
       }
       if (__any_sync(0xffffffffu, stale)) {
 #pragma unroll
-        for (int q = 0; q < Q; ++q)
-          if (needJ[q] && !rec_ok<2>(jw[q], expect))
-            face_wait<2>(upJ + ((long long)(t + kTJ - 1) * TK + g.dk(q)) * W, expect, jw[q], c, abort, tr);
+        for (int r = 0; r < NJ; ++r)
+          if (needJ[r] && !rec_ok<2>(jw[r], expect))
+            face_wait<2>(upJ + ((long long)(t + kTJ - 1) * TK + w * Q + r * PJ) * W, expect, jw[r], c, abort, tr);
         if (needK && !rec_ok<2>(kw, expect))
           face_wait<2>(upK + kface + ((long long)(t + TK - 1) * kTJ + lane) * W, expect, kw, c, abort, tr);
       }
@@ -672,7 +714,7 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
         const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * RBY);
         const T r = sr[q * NT];
         T yS = shfl_up1(ym1[q]);
-        if (lane == 0) yS = needJ[q] ? Face<T>::get(jw[q]) : T(0);
+        if (lane == 0) yS = (g.hasS && act[q]) ? face_row<T, PJ>(jw[q / PJ], q) : T(0);
         T yB;
         if (q > 0) yB = ym1[q > 0 ? q - 1 : 0];
         else if (w > 0) yB = E[(w - 1) * 32 + lane];
@@ -685,12 +727,14 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
       // stores last: y, then the face records (ordered memory operations)
 #pragma unroll
       for (int q = 0; q < Q; ++q)
-        if (act[q]) P.y[B.cell0 + so[q * NT]] = ny[q];
-      uint64_t *pj = myf + ((long long)t * TK + w * Q) * W;
+        if (act[q]) yb[so[q * NT]] = ny[q];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) Face<T>::put_if(pj + q * W, ny[q], ep, lane == kTJ - 1 && g.hasN && act[q]);
+      for (int q = 0; q < Q; q += PJ)
+        face_put<T, PJ>(pjn + q * W, ny, q, ep, lane == kTJ - 1 && g.hasN && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]));
       if (g.eT)  // warp-uniform
-        Face<T>::put_if(myf + kface + ((long long)t * kTJ + lane) * W, ny[Q - 1], ep, g.hasT && act[Q - 1]);
+        Face<T>::put_if(pkn, ny[Q - 1], ep, g.hasT && act[Q - 1]);
+      pjn += (long long)TK * W;
+      pkn += (long long)kTJ * W;
 #pragma unroll
       for (int q = 0; q < Q; ++q) ym1[q] = ny[q];
     }
@@ -713,6 +757,7 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
   constexpr int RBY = 4 * (int)sizeof(T);  // bytes of a U record
   constexpr int C = 32 / Q;
   constexpr int SY = 0, SX = Q;  // scalar slots
+  constexpr int PJ = face_pair<T, Q>();  // rows per J face record
   const SweepCommon &c = P.c;
   const unsigned ep = sweep_prologue(c);
   if (threadIdx.x == 0) s_blk = -1;
@@ -747,7 +792,8 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
       // the walk, cell i = nx-1-lead, published on the producer's step i + lane
       const int lead = min(R + 1, B.nx - 1);
       const int i = B.nx - 1 - lead;
-      slack_gate<W>(g.hasN ? faceJ(dnJ, B, i + g.nkt - 1, g.nkt - 1, W) : nullptr,
+      // (J records of row pairs sit in the slot of the pair's first row)
+      slack_gate<W>(g.hasN ? faceJ(dnJ, B, i + g.nkt - 1, (g.nkt - 1) / PJ * PJ, W) : nullptr,
                     g.hasT ? faceK(dnK, B, i + g.njt - 1, g.njt - 1, W) : nullptr, expect, c, abort, tr);
     }
     int tlo[Q];
@@ -761,6 +807,16 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
     const long long kface = (long long)B.nsteps_max * TK * W;
     int chunk = 0, cb = -C;  // row-base chunk of issue steps [cb, cb + C)
     const int kchunk = g.k0 + w * Q + lane % Q;
+    const T *recb = P.rec + B.cell0 * 4;
+    const T *yb = P.y + B.cell0;
+    T *xb = P.x + B.cell0;
+    double *x64b = UPD64 ? P.x64 + B.cell0 : nullptr;
+    // running face pointers (descending planes): the records read by the
+    // copies of issue step uu (plane last - uu) and written at step u
+    const uint64_t *fjn = dnJ + ((long long)(last - (kTJ - 1)) * TK + w * Q) * W;
+    const uint64_t *fkn = dnK + kface + ((long long)(last - (TK - 1)) * kTJ + lane) * W;
+    uint64_t *pjn = myf + ((long long)last * TK + w * Q) * W;
+    uint64_t *pkn = myf + kface + ((long long)last * kTJ + lane) * W;
 
     auto issue = [&](int uu) {
       if (uu < g.nsteps) {
@@ -777,29 +833,32 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
         uint64_t *fs = fst + (size_t)sl * FS * W;
         int off[Q];
         bool v[Q];
-        long long a[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           off[q] = __shfl_sync(0xffffffffu, chunk, (uu - cb) * Q + q) + g.j;
           v[q] = colq[q] && (unsigned)(t - tlo[q]) < nxu;
-          a[q] = v[q] ? B.cell0 + off[q] : 0;
         }
-        const uint64_t *fj = dnJ + ((long long)(t - (kTJ - 1)) * TK + w * Q) * W;
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
+          const int o = v[q] ? off[q] : 0;
           unsigned char *d = st + ((size_t)q * NT + tid) * RBY;
-          const unsigned char *src = reinterpret_cast<const unsigned char *>(P.rec + a[q] * 4);
+          const unsigned char *src = reinterpret_cast<const unsigned char *>(recb + o * 4);
 #pragma unroll
           for (int z = 0; z < RBY / 16; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v[q]);
-          cp_async_zfill<sizeof(T)>(sc + (SY + q) * NT, P.y + a[q], v[q]);
-          if constexpr (!ZX) cp_async_zfill<sizeof(T)>(sc + (SX + q) * NT, P.x + a[q], v[q]);
-          if constexpr (UPD64) cp_async_zfill<8>(s64 + (size_t)q * NT, P.x64 + a[q], v[q]);
+          cp_async_zfill<sizeof(T)>(sc + (SY + q) * NT, yb + o, v[q]);
+          if constexpr (!ZX) cp_async_zfill<sizeof(T)>(sc + (SX + q) * NT, xb + o, v[q]);
+          if constexpr (UPD64) cp_async_zfill<8>(s64 + (size_t)q * NT, x64b + o, v[q]);
           so[q * NT] = off[q];
-          cp_async_16_if(fs + g.dk(q) * W, fj + q * W, lane == kTJ - 1 && g.hasN && v[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < Q; q += PJ) {
+          const bool vq = PJ == 2 ? (v[q] || v[q + PJ - 1]) : v[q];
+          cp_async_16_if(fs + (w * Q + q) * W, fjn + q * W, lane == kTJ - 1 && g.hasN && vq);
         }
         if (g.eT)  // warp-uniform
-          cp_async_16_if(fs + (TK + lane) * W, dnK + kface + ((long long)(t - (TK - 1)) * kTJ + lane) * W,
-                         g.hasT && v[Q - 1]);
+          cp_async_16_if(fs + (TK + lane) * W, fkn, g.hasT && v[Q - 1]);
+        fjn -= (long long)TK * W;
+        fkn -= (long long)kTJ * W;
       }
       cp_async_commit();
     };
@@ -822,16 +881,20 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
       T *E = exT + (size_t)(u & 1) * NW * 32;
       E[w * 32 + lane] = dE[0];
       __syncthreads();
-      // faces of this step: J (lane 31, per row) and K (last warp, last row)
-      bool act[Q], needJ[Q];
-      uint64_t jw[Q][2], kw[2] = {0, 0};
+      // faces of this step: J (lane 31, per row or row pair) and K (last warp, last row)
+      bool act[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) act[q] = colq[q] && (unsigned)(t - tlo[q]) < nxu;
+      constexpr int NJ = Q / PJ;
+      bool needJ[NJ];
+      uint64_t jw[NJ][2], kw[2] = {0, 0};
       bool stale = false;
 #pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        act[q] = colq[q] && (unsigned)(t - tlo[q]) < nxu;
-        needJ[q] = lane == kTJ - 1 && g.hasN && act[q];
-        staged_words(fs + g.dk(q) * W, jw[q]);
-        stale |= needJ[q] && !rec_ok<2>(jw[q], expect);
+      for (int r = 0; r < NJ; ++r) {
+        const int q = r * PJ;
+        needJ[r] = lane == kTJ - 1 && g.hasN && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]);
+        staged_words(fs + (w * Q + q) * W, jw[r]);
+        stale |= needJ[r] && !rec_ok<2>(jw[r], expect);
       }
       const bool needK = g.eT && g.hasT && act[Q - 1];
       if (g.eT) {
@@ -840,9 +903,9 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
       }
       if (__any_sync(0xffffffffu, stale)) {
 #pragma unroll
-        for (int q = 0; q < Q; ++q)
-          if (needJ[q] && !rec_ok<2>(jw[q], expect))
-            face_wait<2>(dnJ + ((long long)(t - (kTJ - 1)) * TK + g.dk(q)) * W, expect, jw[q], c, abort, tr);
+        for (int r = 0; r < NJ; ++r)
+          if (needJ[r] && !rec_ok<2>(jw[r], expect))
+            face_wait<2>(dnJ + ((long long)(t - (kTJ - 1)) * TK + w * Q + r * PJ) * W, expect, jw[r], c, abort, tr);
         if (needK && !rec_ok<2>(kw, expect))
           face_wait<2>(dnK + kface + ((long long)(t - (TK - 1)) * kTJ + lane) * W, expect, kw, c, abort, tr);
       }
@@ -852,7 +915,7 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
       for (int q = 0; q < Q; ++q) {
         const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * RBY);
         T dN = shfl_dn1(dE[q]);
-        if (lane == kTJ - 1) dN = needJ[q] ? Face<T>::get(jw[q]) : T(0);
+        if (lane == kTJ - 1) dN = (g.hasN && act[q]) ? face_row<T, PJ>(jw[q / PJ], q) : T(0);
         T dT;
         if (q < Q - 1) dT = dE[q < Q - 1 ? q + 1 : 0];
         else if (w < NW - 1) dT = E[(w + 1) * 32 + lane];
@@ -868,18 +931,20 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
       // stores last: the update, then the face records (ordered memory operations)
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        const long long a = B.cell0 + so[q * NT];
+        const int o = so[q * NT];
         if constexpr (UPD64) {
-          if (act[q]) P.x64[a] = s64[(size_t)q * NT] + (double)xv[q];
+          if (act[q]) x64b[o] = s64[(size_t)q * NT] + (double)xv[q];
         } else {
-          if (act[q]) P.x[a] = xv[q];
+          if (act[q]) xb[o] = xv[q];
         }
       }
-      uint64_t *pj = myf + ((long long)t * TK + w * Q) * W;
 #pragma unroll
-      for (int q = 0; q < Q; ++q) Face<T>::put_if(pj + q * W, nd[q], ep, lane == 0 && g.hasS && act[q]);
+      for (int q = 0; q < Q; q += PJ)
+        face_put<T, PJ>(pjn + q * W, nd, q, ep, lane == 0 && g.hasS && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]));
       if (g.eB)  // warp-uniform
-        Face<T>::put_if(myf + kface + ((long long)t * kTJ + lane) * W, nd[0], ep, g.hasB && act[0]);
+        Face<T>::put_if(pkn, nd[0], ep, g.hasB && act[0]);
+      pjn -= (long long)TK * W;
+      pkn -= (long long)kTJ * W;
 #pragma unroll
       for (int q = 0; q < Q; ++q) dE[q] = nd[q];
     }
