@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--serve-max-n", type=int, default=48, help="largest cube edge of a served request")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-block batched-mesh measurement")
+    ap.add_argument("--no-small", action="store_true", help="skip the 32^3 solve-latency measurement")
+    ap.add_argument("--large", action="store_true",
+                    help="also solve the 384^3 Peclet-10 block with FP32 coefficients (alpha 0.5 and 0.92)")
     ap.add_argument("--batched-iters", type=int, default=12,
                     help="corrections (refined) / iterations (fp64) timed on the batched mesh")
     return ap.parse_args()
@@ -416,8 +419,12 @@ def run_gb300(args):
     }
     if ttol:
         line["time_to_1e-8"] = ttol
+    if not args.no_small and world == 1:
+        line["small"] = small(args, local)
     if not args.no_batched and world == 1:
         line["batched"] = batched(args, local)
+    if args.large and world == 1:
+        line["large"] = large(args, local)
     if args.serve_requests > 0 and world == 1:
         line["serving"] = serving(args, local)
     print(json.dumps(line), flush=True)
@@ -426,6 +433,94 @@ def run_gb300(args):
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def _solve_timed(plan, x, stream, rtol, max_iters, reps=1):
+    """Solve from x = 0, timed with CUDA events on the plan's stream (median
+    of reps); returns (ms, iterations, relres, converged)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    for _ in range(reps):
+        x.zero_()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        it, rel, conv = plan.solve(rtol, max_iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out.append((e0.elapsed_time(e1), it, rel, conv))
+    out.sort(key=lambda r: r[0])
+    return out[len(out) // 2]
+
+
+def small(args, local):
+    """The 32^3 convection-diffusion block (time term 0.01): latency of one
+    solve to 1e-8 on a factored plan (x from 0, CUDA graphs), plain FP64 vs
+    FP32-refined, median of 9."""
+    import torch
+
+    from paper_1303_4538_gb300 import sip
+    from paper_1303_4538_gb300 import workloads as W
+
+    blk = W.convdiff_32cube()
+    stream = torch.cuda.current_stream()
+    ctx = sip.Context(local, stream.cuda_stream)
+    A = [torch.from_numpy(c).cuda() for c in blk.coef_list()]
+    b = torch.from_numpy(blk.b).cuda()
+    x = torch.zeros(blk.n, dtype=torch.float64, device="cuda")
+    desc = sip.make_desc(blk.nx, blk.ny, blk.nz, A, b, x)
+    out = {"workload": "convdiff_32cube", "cells": blk.n, "alpha": 0.92, "rtol": 1e-8}
+    for name, mode in (("f64", sip.SIP_MODE_F64), ("f32_refined", sip.SIP_MODE_F32_REFINED)):
+        plan = sip.Plan(ctx, [desc], sip.default_options(mode=mode, graphs=1))
+        _solve_timed(plan, x, stream, 1e-8, 1000)
+        ms, it, rel, conv = _solve_timed(plan, x, stream, 1e-8, 1000, reps=9)
+        out[name] = {"solve_ms": round(ms, 3), "iterations": it, "relres": rel, "converged": bool(conv)}
+        plan.close()
+    ctx.close()
+    return out
+
+
+def large(args, local):
+    """The 384^3 convection-diffusion block with median cell Peclet 10,
+    coefficients stored in FP32 (factors FP32, residual and refinement FP64):
+    time to 1e-8 of the refined solver at alpha 0.5 against plain FP64 SIP
+    (FP64 coefficients) at alpha 0.5, and the first 40 FP64 iterations at
+    alpha 0.92 (relres history: SIP diverges there)."""
+    import torch
+
+    from paper_1303_4538_gb300 import sip
+    from paper_1303_4538_gb300 import workloads as W
+
+    blk = W.convdiff_pe10_384cube()
+    stream = torch.cuda.current_stream()
+    ctx = sip.Context(local, stream.cuda_stream)
+    A = [torch.from_numpy(c).to("cuda", torch.float32) for c in blk.coef_list()]
+    b = torch.from_numpy(blk.b).cuda()
+    x = torch.zeros(blk.n, dtype=torch.float64, device="cuda")
+    desc = sip.make_desc(blk.nx, blk.ny, blk.nz, A, b, x, coef_dtype=1)
+    out = {"workload": "convdiff_pe10_384cube", "cells": blk.n, "coefficients": "f32"}
+    plan = sip.Plan(ctx, [desc], sip.default_options(mode=sip.SIP_MODE_F32_REFINED, alpha=0.5, graphs=1))
+    ms, it, rel, conv = _solve_timed(plan, x, stream, 1e-8, 3000)
+    out["f32_refined_alpha05"] = {"seconds": round(ms / 1e3, 3), "corrections": it, "sip_iterations": it * 4,
+                                  "relres": rel, "converged": bool(conv)}
+    plan.close()
+    del A
+    torch.cuda.empty_cache()
+    A = [torch.from_numpy(c).cuda() for c in blk.coef_list()]
+    desc = sip.make_desc(blk.nx, blk.ny, blk.nz, A, b, x)
+    plan = sip.Plan(ctx, [desc], sip.default_options(mode=sip.SIP_MODE_F64, alpha=0.5, graphs=1))
+    ms, it, rel, conv = _solve_timed(plan, x, stream, 1e-8, 5000)
+    out["f64_alpha05"] = {"seconds": round(ms / 1e3, 3), "iterations": it, "relres": rel, "converged": bool(conv),
+                          "coefficients": "f64"}
+    plan.close()
+    plan = sip.Plan(ctx, [desc], sip.default_options(mode=sip.SIP_MODE_F64, alpha=0.92, graphs=1))
+    x.zero_()
+    plan.iterate(40)
+    h = plan.history()
+    out["f64_alpha092_relres"] = {"min": min(h), "at_40": h[-1], "diverges": bool(h[-1] > 4 * min(h))}
+    plan.close()
+    ctx.close()
+    return out
 
 
 def batched(args, local):
