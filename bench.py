@@ -52,8 +52,7 @@ ALGO_BYTES = {
     "fwd32": 6 * 4,
     "bwd32": 6 * 4,                    # UE UN UT y d in, d out
     "bwd32_x0": 5 * 4,                 # UE UN UT y in, d out
-    "bwd32_upd64": 5 * 4 + 16,         # UE UN UT y d in, x64 in/out
-    "bwd32_x0_upd64": 4 * 4 + 16,      # UE UN UT y in, x64 in/out
+    "update64": 4 + 16,                # d in, x64 in/out (refinement update)
 }
 
 

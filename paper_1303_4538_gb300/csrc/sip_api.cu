@@ -315,16 +315,15 @@ int enqueue_forward(sip_plan *p, int kind, const T *r, T *y) {
   return SIP_OK;
 }
 
-// Backward substitution d = U^-1 y and the update (x <- x + d, or x64 += d).
+// Backward substitution d = U^-1 y and the update x <- x + d.
 template <typename T>
-int enqueue_backward(sip_plan *p, int kind, const T *y, T *x, double *x64) {
+int enqueue_backward(sip_plan *p, int kind, const T *y, T *x) {
   sip_ctx *ctx = p->ctx;
   BwdParams<T> b;
   b.c = common(p, true, 1, 0, 1, kind);
   b.rec = (const T *)p->recB;
   b.y = y;
   b.x = x;
-  b.x64 = x64;
   CU(launch(p, kind, b));
   return SIP_OK;
 }
@@ -343,12 +342,13 @@ int enqueue_iter_f64(sip_plan *p) {
   if (int rc = enqueue_resid(p, K_RES64, (const double *)p->recA, b, p->x64, p->y64, true)) return rc;
   if (int rc = enqueue_relres(p)) return rc;
   if (int rc = enqueue_forward(p, K_FWD64, p->y64, p->y64)) return rc;
-  return enqueue_backward(p, K_BWD64, p->y64, p->x64, (double *)nullptr);
+  return enqueue_backward(p, K_BWD64, p->y64, p->x64);
 }
 
 // One FP64 correction of the refinement: FP64 residual (+ stop rule), then
-// m FP32 SIP iterations on A d = r from d = 0, the last adding d to x.
+// m FP32 SIP iterations on A d = r from d = 0, then x64 += (double) d.
 int enqueue_iter_refined(sip_plan *p) {
+  sip_ctx *ctx = p->ctx;
   const int m = std::max(1, p->opt.inner_iters);
   if (int rc = enqueue_halo(p)) return rc;
   const double *bres = p->beff64 ? p->beff64 : p->b64;
@@ -357,7 +357,7 @@ int enqueue_iter_refined(sip_plan *p) {
   if (rc) return rc;
   if ((rc = enqueue_relres(p))) return rc;
   for (int q = 0; q < m; ++q) {
-    const bool first = q == 0, lastq = q == m - 1;
+    const bool first = q == 0;
     if (first) {
       rc = enqueue_forward(p, K_FWD32, (const float *)p->r32, p->y32);  // d = 0: the residual is r
     } else {
@@ -366,8 +366,11 @@ int enqueue_iter_refined(sip_plan *p) {
       if (!rc) rc = enqueue_forward(p, K_FWD32, (const float *)p->y32, p->y32);
     }
     if (rc) return rc;
-    const int bk = first ? (lastq ? K_BWD32ZU : K_BWD32Z) : (lastq ? K_BWD32U : K_BWD32);
-    if ((rc = enqueue_backward(p, bk, (const float *)p->y32, p->d32, lastq ? p->x64 : nullptr))) return rc;
+    if ((rc = enqueue_backward(p, first ? K_BWD32Z : K_BWD32, (const float *)p->y32, p->d32))) return rc;
+  }
+  {
+    ProfScope ps(p, K_UPD64);
+    CU(launch_update64(p->d32, p->x64, p->ncells, p->ctl, ctx->stream));
   }
   return SIP_OK;
 }
@@ -384,7 +387,7 @@ int enqueue_iter_f32(sip_plan *p) {
     return rc;
   if (int rc = enqueue_relres(p)) return rc;
   if (int rc = enqueue_forward(p, K_FWD32, (const float *)p->y32, p->y32)) return rc;
-  return enqueue_backward(p, K_BWD32, (const float *)p->y32, p->d32, (double *)nullptr);
+  return enqueue_backward(p, K_BWD32, (const float *)p->y32, p->d32);
 }
 
 int enqueue_iter(sip_plan *p) {
@@ -478,7 +481,7 @@ int end_sequence(sip_plan *p) {
 std::vector<int> plan_kinds(int mode) {
   if (mode == SIP_MODE_F64) return {K_FACTOR, K_FWD64, K_BWD64};
   if (mode == SIP_MODE_F32) return {K_FACTOR32, K_FWD32, K_BWD32};
-  return {K_FACTOR32, K_FWD32, K_BWD32, K_BWD32Z, K_BWD32U, K_BWD32ZU};
+  return {K_FACTOR32, K_FWD32, K_BWD32, K_BWD32Z};
 }
 
 // Tile shape: rows per thread Q and warps NW (tile = 32 x Q*NW), stage depth
@@ -1170,9 +1173,8 @@ int sip_launch_count(sip_plan *p, int64_t *count_out) {
 }
 
 const char *sip_kernel_name(int kind) {
-  static const char *names[] = {"factor",      "fwd64",    "bwd64",        "factor32",     "fwd32",
-                                "bwd32",       "bwd32_x0", "bwd32_upd64",  "bwd32_x0_upd64", "resid64",
-                                "resid32",     "resid32_norm", "resid64_r32", "utility"};
+  static const char *names[] = {"factor", "fwd64",        "bwd64",       "factor32", "fwd32",  "bwd32", "bwd32_x0",
+                                "resid64", "resid32", "resid32_norm", "resid64_r32", "update64", "utility"};
   static_assert(sizeof(names) / sizeof(names[0]) == K_NKINDS + 1, "kernel names");
   if (kind < 0 || kind > K_NKINDS) return nullptr;
   return names[kind];

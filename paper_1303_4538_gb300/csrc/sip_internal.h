@@ -108,7 +108,6 @@ struct BwdParams {
   const T *rec;  // backward records
   const T *y;
   T *x;          // correction accumulated in place (x <- x + d)
-  double *x64;   // refined mode, last inner iteration: x64 += (double) x
 };
 
 template <typename TF>
@@ -152,6 +151,8 @@ cudaError_t launch_finalize(const double *partials, int n, Ctl *ctl, double *his
 cudaError_t launch_set_ctl(Ctl *ctl, double rtol, int max_iters, cudaStream_t st);
 cudaError_t launch_cast_f64_f32(const double *src, float *dst, long long n, cudaStream_t st);
 cudaError_t launch_cast_f32_f64(const float *src, double *dst, long long n, cudaStream_t st);
+// refinement update x64 += (double) d over n plan cells; nothing once ctl->done
+cudaError_t launch_update64(const float *d, double *x64, long long n, const Ctl *ctl, cudaStream_t st);
 cudaError_t launch_export_factors(const void *recF, const void *recB, int is_f32, double *const out[7],
                                   const DevBlock &hb, cudaStream_t st);
 

@@ -12,10 +12,8 @@ static const void *pick32(int kind) {
   switch (kind) {
     case K_FACTOR32: return (const void *)k_factor<float, Q, R>;
     case K_FWD32: return (const void *)k_forward<float, Q, R>;
-    case K_BWD32: return (const void *)k_backward<float, false, false, Q, R>;
-    case K_BWD32Z: return (const void *)k_backward<float, true, false, Q, R>;
-    case K_BWD32U: return (const void *)k_backward<float, false, true, Q, R>;
-    case K_BWD32ZU: return (const void *)k_backward<float, true, true, Q, R>;
+    case K_BWD32: return (const void *)k_backward<float, false, Q, R>;
+    case K_BWD32Z: return (const void *)k_backward<float, true, Q, R>;
     default: return nullptr;
   }
 }

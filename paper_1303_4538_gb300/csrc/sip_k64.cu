@@ -11,7 +11,7 @@ static const void *pick64(int kind) {
   switch (kind) {
     case K_FACTOR: return (const void *)k_factor<double, Q, R>;
     case K_FWD64: return (const void *)k_forward<double, Q, R>;
-    case K_BWD64: return (const void *)k_backward<double, false, false, Q, R>;
+    case K_BWD64: return (const void *)k_backward<double, false, Q, R>;
     default: return nullptr;
   }
 }

@@ -15,16 +15,14 @@ enum KernelKind {
   K_FWD32,        // FP32 forward substitution
   K_BWD32,        // FP32 backward + update
   K_BWD32Z,       // FP32 backward with x = 0 on entry
-  K_BWD32U,       // FP32 backward + update, then x64 += x
-  K_BWD32ZU,      // x = 0 on entry, then x64 += x
   // row-parallel residual r = b - A x (sip_resrow.cu; not ticketed, no Q/R)
   K_RES64,        // FP64: r into the substitution buffer, with the norm
   K_RES32,        // FP32, no norm (inner iterations of the refinement)
   K_RES32N,       // FP32 with the norm (single-precision mode)
   K_RES64R,       // FP64 residual of the refinement (A in FP64 or FP32), r rounded to FP32, norm
+  K_UPD64,        // refinement update x64 += (double) d (element-wise)
   K_NKINDS
 };
-constexpr bool kind_is_row(int kind) { return kind >= K_RES64 && kind < K_NKINDS; }
 
 constexpr int kQs[2] = {2, 4};
 constexpr int kRs[3] = {2, 4, 6};  // 2: the factorisation only (wide tiles)

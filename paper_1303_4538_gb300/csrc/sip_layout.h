@@ -4,7 +4,7 @@
 // Every sweep kernel's dynamic shared memory is
 //   [ PO + F tables of the current block ]
 //   [ R stages: per step the staged records of the thread's Q rows, then
-//     scalar slots (r; y and x; the FP64 iterate of the refinement), then the
+//     scalar slots (r; y and x), then the
 //     cells' block-local offsets (kept from the issue for the store) ]
 //   [ exchange between neighbouring warps, double buffered ]
 //   [ R stages of face records consumed by the tile's edge threads ]
@@ -19,7 +19,6 @@ struct SweepLayout {
   size_t tab;    // bytes of the PO/F tables
   size_t step;   // bytes of one stage
   size_t rec;    // bytes of the staged records inside a stage (Q * NT * rsb)
-  size_t aux;    // bytes of an auxiliary 8-byte region after the records (x64)
   size_t off;    // offset inside a stage of the cells' block-local offsets (Q * NT ints)
   size_t exch;   // bytes of the exchange area
   size_t faces;  // bytes of the face ring
@@ -39,7 +38,6 @@ __host__ __device__ inline SweepLayout fwd_layout(int esize, int Q, int R, int N
   L.fs = TK + 32;
   L.tab = lay_a16((size_t)tab_ints * 4);
   L.rec = (size_t)Q * NT * L.rsb;
-  L.aux = 0;
   L.off = L.rec + (size_t)L.nsv * NT * esize;
   L.step = lay_a16(L.off + (size_t)Q * NT * 4);
   L.exch = lay_a16((size_t)2 * NW * 32 * esize);
@@ -48,8 +46,8 @@ __host__ __device__ inline SweepLayout fwd_layout(int esize, int Q, int R, int N
   return L;
 }
 
-// backward sweep: record [UE UN UT 0]; scalars y, x per row; optional x64 per row
-__host__ __device__ inline SweepLayout bwd_layout(int esize, bool zx, bool upd64, int Q, int R, int NT, int tab_ints) {
+// backward sweep: record [UE UN UT 0]; scalars y, x per row
+__host__ __device__ inline SweepLayout bwd_layout(int esize, bool zx, int Q, int R, int NT, int tab_ints) {
   SweepLayout L{};
   const int NW = NT / 32, TK = NW * Q;
   L.rsb = 4 * esize;
@@ -57,8 +55,7 @@ __host__ __device__ inline SweepLayout bwd_layout(int esize, bool zx, bool upd64
   L.fs = TK + 32;
   L.tab = lay_a16((size_t)tab_ints * 4);
   L.rec = (size_t)Q * NT * L.rsb;
-  L.aux = upd64 ? (size_t)Q * NT * 8 : 0;
-  L.off = L.rec + L.aux + (size_t)L.nsv * NT * esize;
+  L.off = L.rec + (size_t)L.nsv * NT * esize;
   L.step = lay_a16(L.off + (size_t)Q * NT * 4);
   L.exch = lay_a16((size_t)2 * NW * 32 * esize);
   L.faces = (size_t)R * L.fs * 2 * 8;
@@ -75,7 +72,6 @@ __host__ __device__ inline SweepLayout fac_layout(int Q, int R, int NT, int tab_
   L.fs = TK + 32;
   L.tab = lay_a16((size_t)tab_ints * 4);
   L.rec = (size_t)Q * NT * L.rsb;
-  L.aux = 0;
   L.step = L.rec;
   L.exch = lay_a16((size_t)2 * 3 * NW * 32 * 8);
   L.faces = (size_t)R * L.fs * 6 * 8;

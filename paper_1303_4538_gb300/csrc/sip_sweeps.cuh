@@ -747,9 +747,8 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
 // =========================================================== backward sweep
 // backward3d with the update: d_P = y_P - UE d_E - UN d_N - UT d_T
 // (descending planes), x_P <- x_P + d_P.  ZX: x = 0 on entry (x_P <- d_P).
-// UPD64 (refined mode, last inner iteration): x64_P += (double) x_P instead
-// of storing x_P.  Backward step u processes local plane t = last - u.
-template <typename T, bool ZX, bool UPD64, int Q, int R>
+// Backward step u processes local plane t = last - u.
+template <typename T, bool ZX, int Q, int R>
 __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_claim, s_blk;
@@ -765,7 +764,7 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
   if (__syncthreads_or(c.ctl->done || ld_relaxed(c.status) != DEV_OK)) return;
   const unsigned expect = ep + (c.stall ? 0x40000000u : 0u);
   const int NT = blockDim.x, tid = threadIdx.x;
-  const SweepLayout L = bwd_layout((int)sizeof(T), ZX, UPD64, Q, R, NT, c.tab_ints);
+  const SweepLayout L = bwd_layout((int)sizeof(T), ZX, Q, R, NT, c.tab_ints);
   int *sPO = reinterpret_cast<int *>(smem_raw);
   unsigned char *stage = smem_raw + L.tab;
   T *exT = reinterpret_cast<T *>(stage + (size_t)R * L.step);  // [2][NW][32]: d of a warp's first row
@@ -810,7 +809,6 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
     const T *recb = P.rec + B.cell0 * 4;
     const T *yb = P.y + B.cell0;
     T *xb = P.x + B.cell0;
-    double *x64b = UPD64 ? P.x64 + B.cell0 : nullptr;
     // running face pointers (descending planes): the records read by the
     // copies of issue step uu (plane last - uu) and written at step u
     const uint64_t *fjn = dnJ + ((long long)(last - (kTJ - 1)) * TK + w * Q) * W;
@@ -827,8 +825,7 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
         const int t = last - uu;
         const int sl = uu % R;
         unsigned char *st = stage + (size_t)sl * L.step;
-        double *s64 = reinterpret_cast<double *>(st + L.rec) + tid;
-        T *sc = reinterpret_cast<T *>(st + L.rec + L.aux) + tid;
+        T *sc = reinterpret_cast<T *>(st + L.rec) + tid;
         int *so = reinterpret_cast<int *>(st + L.off) + tid;
         uint64_t *fs = fst + (size_t)sl * FS * W;
         int off[Q];
@@ -847,7 +844,6 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
           for (int z = 0; z < RBY / 16; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v[q]);
           cp_async_zfill<sizeof(T)>(sc + (SY + q) * NT, yb + o, v[q]);
           if constexpr (!ZX) cp_async_zfill<sizeof(T)>(sc + (SX + q) * NT, xb + o, v[q]);
-          if constexpr (UPD64) cp_async_zfill<8>(s64 + (size_t)q * NT, x64b + o, v[q]);
           so[q * NT] = off[q];
         }
 #pragma unroll
@@ -873,8 +869,7 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
       cp_async_wait<R - 1>();
       const int sl = u % R;
       const unsigned char *st = stage + (size_t)sl * L.step;
-      const double *s64 = reinterpret_cast<const double *>(st + L.rec) + tid;
-      const T *sc = reinterpret_cast<const T *>(st + L.rec + L.aux) + tid;
+      const T *sc = reinterpret_cast<const T *>(st + L.rec) + tid;
       const int *so = reinterpret_cast<const int *>(st + L.off) + tid;
       const uint64_t *fs = fst + (size_t)sl * FS * W;
       const int t = last - u;
@@ -930,14 +925,8 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
       }
       // stores last: the update, then the face records (ordered memory operations)
 #pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const int o = so[q * NT];
-        if constexpr (UPD64) {
-          if (act[q]) x64b[o] = s64[(size_t)q * NT] + (double)xv[q];
-        } else {
-          if (act[q]) xb[o] = xv[q];
-        }
-      }
+      for (int q = 0; q < Q; ++q)
+        if (act[q]) xb[so[q * NT]] = xv[q];
 #pragma unroll
       for (int q = 0; q < Q; q += PJ)
         face_put<T, PJ>(pjn + q * W, nd, q, ep, lane == 0 && g.hasS && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]));

@@ -21,12 +21,10 @@ size_t kernel_smem(int kind, int Q, int R, int NT, int tab) {
     case K_FACTOR:
     case K_FACTOR32: return fac_layout(Q, R, NT, tab).total;
     case K_FWD64: return fwd_layout(8, Q, R, NT, tab).total;
-    case K_BWD64: return bwd_layout(8, false, false, Q, R, NT, tab).total;
+    case K_BWD64: return bwd_layout(8, false, Q, R, NT, tab).total;
     case K_FWD32: return fwd_layout(4, Q, R, NT, tab).total;
-    case K_BWD32: return bwd_layout(4, false, false, Q, R, NT, tab).total;
-    case K_BWD32Z: return bwd_layout(4, true, false, Q, R, NT, tab).total;
-    case K_BWD32U: return bwd_layout(4, false, true, Q, R, NT, tab).total;
-    case K_BWD32ZU: return bwd_layout(4, true, true, Q, R, NT, tab).total;
+    case K_BWD32: return bwd_layout(4, false, Q, R, NT, tab).total;
+    case K_BWD32Z: return bwd_layout(4, true, Q, R, NT, tab).total;
     default: return 0;
   }
 }
@@ -255,6 +253,31 @@ cudaError_t launch_cast_f64_f32(const double *src, float *dst, long long n, cuda
 }
 cudaError_t launch_cast_f32_f64(const float *src, double *dst, long long n, cudaStream_t st) {
   k_cast_f32_f64<<<util_grid(n), 256, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+// The refinement's update x64 += (double) d (d: the FP32 correction of the
+// last inner iteration), four cells per thread with 16-byte accesses.
+__global__ void k_update64(const float *d, double *x64, long long n, const Ctl *ctl) {
+  if (ctl->done) return;
+  const long long n4 = n / 4;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += stride) {
+    const float4 dv = reinterpret_cast<const float4 *>(d)[q];
+    double2 *xp = reinterpret_cast<double2 *>(x64) + 2 * q;
+    double2 a = xp[0], b = xp[1];
+    a.x += (double)dv.x;
+    a.y += (double)dv.y;
+    b.x += (double)dv.z;
+    b.y += (double)dv.w;
+    xp[0] = a;
+    xp[1] = b;
+  }
+  for (long long q = 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += stride)
+    x64[q] += (double)d[q];
+}
+cudaError_t launch_update64(const float *d, double *x64, long long n, const Ctl *ctl, cudaStream_t st) {
+  k_update64<<<util_grid((n + 3) / 4), 256, 0, st>>>(d, x64, n, ctl);
   return cudaGetLastError();
 }
 
