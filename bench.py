@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=3)
     ap.add_argument("--no-ttol", action="store_true", help="skip the time-to-1e-8 solves")
+    ap.add_argument("--no-inner-sweep", action="store_true",
+                    help="time-to-1e-8 of the refined form with the default inner count only (skip m = 1, 2, 8)")
+    ap.add_argument("--small-solves", type=int, default=100, help="solves of the 32^3 latency measurement")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving measurement (0: skip)")
     ap.add_argument("--serve-max-n", type=int, default=48, help="largest cube edge of a served request")
     ap.add_argument("--serve-slots", type=int, default=4)
@@ -176,6 +179,33 @@ def peaks():
 
 
 # ------------------------------------------------------------------ oracle
+def host_cpu():
+    """CPU model and core count of this host (for the oracle timing)."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu part", "hardware") and ":" in line:
+                model = line.split(":", 1)[1].strip()
+                if key == "model name":
+                    break
+    except OSError:
+        pass
+    parts = {"0xd4f": "Arm Neoverse V2 (Grace)", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1"}
+    return {"model": parts.get(model, model), "nproc": os.cpu_count()}
+
+
+# The paper's own figures for this path (CPU, FP64): context, not a target.
+PAPER_CPU = {
+    "hardware": "Intel Xeon X5650 (Westmere), 1 core, Intel Fortran 12.1",
+    "resforward3d_MB_per_s": 7116, "backward3d_MB_per_s": 7025, "lu3d_MB_per_s": 4204,
+    "resforward3d_ms_per_call": round(56.48e3 / 7500, 2),
+    "source": "arXiv:1303.4538 Tables 1 and 4 (profile of test case I, implicit, serial)",
+    "note": "no cell counts per call are given, so no MLUP/s; about 0.5 M cells per call at 7.1 GB/s would be "
+            "60-70 MLUP/s (order of magnitude only)",
+}
+
+
 def cpu_baseline(blk, iters: int):
     import numpy as np
     import oracle
@@ -289,8 +319,7 @@ def run_gb300(args):
     e1.record(stream)
     torch.cuda.synchronize()
     factor_ms_d = e0.elapsed_time(e1)
-    del A
-    torch.cuda.empty_cache()
+    # A stays allocated: the inner-count sweep of the time-to-1e-8 factors more plans from it
 
     def step(plan):
         x.zero_()
@@ -347,7 +376,13 @@ def run_gb300(args):
 
     ttol = {}
     if not args.no_ttol:
-        for name, plan, inner in (("f32_refined", plan_r, args.inner), ("f64", plan_d, 1)):
+        runs = [("f32_refined", plan_r, args.inner, False), ("f64", plan_d, 1, False)]
+        # the refined form with other numbers of FP32 iterations per FP64 correction
+        for m in (1, 2, 8):
+            if m != args.inner and not args.no_inner_sweep:
+                runs.append((f"f32_refined_m{m}", sip.Plan(ctx, [desc], sip.default_options(
+                    mode=sip.SIP_MODE_F32_REFINED, inner_iters=m)), m, True))
+        for name, plan, inner, own in runs:
             barrier()
             x.zero_()
             e0.record(stream)
@@ -356,6 +391,8 @@ def run_gb300(args):
             barrier()
             ttol[name] = {"seconds": e0.elapsed_time(e1) / 1e3, "iterations": it, "sip_iterations": it * inner,
                           "relres": rel, "converged": conv}
+            if own:
+                plan.close()
 
     def rates(ms, iters):
         return N * iters / (ms / 1e3) / 1e6
@@ -395,7 +432,7 @@ def run_gb300(args):
         v, dt = cpu_baseline(blk, args.cpu_iters)
         cpu = {"value": v, "unit": "MLUP/s", "cores": 1, "kind": "oracle",
                "sample": f"{args.cpu_iters} FP64 SIP iterations of the {args.n}^3 Poisson block "
-                         f"({dt:.1f} s, plain C, 1 thread)"}
+                         f"({dt:.1f} s, plain C, 1 thread)", "host": host_cpu()}
     line = {
         "metric": METRIC, "value": round(val_r, 1), "unit": "MLUP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_r / args.steps, 3), "higher_is_better": True,
@@ -406,6 +443,7 @@ def run_gb300(args):
                    f"{plan_r.nbytes() / 1e9:.2f} GB)", "step": "sip_solve on the factored plan, x reset to 0"},
         "roofline": roofline(prof_r),
         "cpu_baseline": cpu,
+        "paper_cpu_context": PAPER_CPU,
         "e2e": {"value": round(val_e2e, 1), "unit": "MLUP/s", "h2d_bytes_per_step": 2 * N * 8,
                 "d2h_bytes_per_step": N * 8},
         "gpu_launches": int(launches_r),
@@ -455,7 +493,8 @@ def _solve_timed(plan, x, stream, rtol, max_iters, reps=1):
 def small(args, local):
     """The 32^3 convection-diffusion block (time term 0.01): latency of one
     solve to 1e-8 on a factored plan (x from 0, CUDA graphs), plain FP64 vs
-    FP32-refined, median of 9."""
+    FP32-refined: p50/p99 of the host-observed call over --small-solves
+    solves, and the device time (CUDA events, median of 5)."""
     import torch
 
     from paper_1303_4538_gb300 import sip
@@ -468,12 +507,24 @@ def small(args, local):
     b = torch.from_numpy(blk.b).cuda()
     x = torch.zeros(blk.n, dtype=torch.float64, device="cuda")
     desc = sip.make_desc(blk.nx, blk.ny, blk.nz, A, b, x)
-    out = {"workload": "convdiff_32cube", "cells": blk.n, "alpha": 0.92, "rtol": 1e-8}
+    out = {"workload": "convdiff_32cube", "cells": blk.n, "alpha": 0.92, "rtol": 1e-8, "solves": args.small_solves}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for name, mode in (("f64", sip.SIP_MODE_F64), ("f32_refined", sip.SIP_MODE_F32_REFINED)):
         plan = sip.Plan(ctx, [desc], sip.default_options(mode=mode, graphs=1))
         _solve_timed(plan, x, stream, 1e-8, 1000)
-        ms, it, rel, conv = _solve_timed(plan, x, stream, 1e-8, 1000, reps=9)
-        out[name] = {"solve_ms": round(ms, 3), "iterations": it, "relres": rel, "converged": bool(conv)}
+        lat = []
+        for _ in range(args.small_solves):
+            # one solve as a caller sees it: x reset, solve (returns on the host), result read
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x.zero_()
+            it, rel, conv = plan.solve(1e-8, 1000)
+            lat.append((time.perf_counter() - t0) * 1e3)
+        ms_dev, _, _, _ = _solve_timed(plan, x, stream, 1e-8, 1000, reps=5)
+        lat.sort()
+        out[name] = {"p50_ms": round(lat[len(lat) // 2], 3), "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
+                     "device_ms": round(ms_dev, 3), "iterations": it, "relres": rel, "converged": bool(conv),
+                     "MLUP_per_s": round(blk.n * it * (4 if mode == sip.SIP_MODE_F32_REFINED else 1) / ms_dev / 1e3, 1)}
         plan.close()
     ctx.close()
     return out
@@ -500,8 +551,11 @@ def large(args, local):
     out = {"workload": "convdiff_pe10_384cube", "cells": blk.n, "coefficients": "f32"}
     plan = sip.Plan(ctx, [desc], sip.default_options(mode=sip.SIP_MODE_F32_REFINED, alpha=0.5, graphs=1))
     ms, it, rel, conv = _solve_timed(plan, x, stream, 1e-8, 3000)
+    import numpy as np
+    xs = x.cpu().numpy()
     out["f32_refined_alpha05"] = {"seconds": round(ms / 1e3, 3), "corrections": it, "sip_iterations": it * 4,
-                                  "relres": rel, "converged": bool(conv)}
+                                  "relres": rel, "converged": bool(conv),
+                                  "err_vs_xstar": float(np.linalg.norm(xs - blk.xstar) / np.linalg.norm(blk.xstar))}
     plan.close()
     del A
     torch.cuda.empty_cache()
@@ -509,8 +563,10 @@ def large(args, local):
     desc = sip.make_desc(blk.nx, blk.ny, blk.nz, A, b, x)
     plan = sip.Plan(ctx, [desc], sip.default_options(mode=sip.SIP_MODE_F64, alpha=0.5, graphs=1))
     ms, it, rel, conv = _solve_timed(plan, x, stream, 1e-8, 5000)
+    xs = x.cpu().numpy()
     out["f64_alpha05"] = {"seconds": round(ms / 1e3, 3), "iterations": it, "relres": rel, "converged": bool(conv),
-                          "coefficients": "f64"}
+                          "coefficients": "f64",
+                          "err_vs_xstar": float(np.linalg.norm(xs - blk.xstar) / np.linalg.norm(blk.xstar))}
     plan.close()
     plan = sip.Plan(ctx, [desc], sip.default_options(mode=sip.SIP_MODE_F64, alpha=0.92, graphs=1))
     x.zero_()
