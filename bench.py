@@ -581,7 +581,8 @@ def large(args, local):
 def batched(args, local):
     """The 64-block block-structured mesh (~20 M cells, sizes 24..128 per
     axis, convection-diffusion, x-chained interfaces with device-side lagged
-    halo coupling): one plan over all blocks, CUDA graphs.  MLUP/s over a fixed
+    halo coupling): one plan over all blocks, CUDA graphs, tile shape from the
+    measuring autotuner (plan creation, outside the timed region).  MLUP/s over a fixed
     number of corrections / iterations (x reset to 0, timed with CUDA events
     on the plan's stream) and the time to the 1e-8 coupled relative residual
     for the FP32-refined and the plain FP64 solver."""
@@ -612,7 +613,8 @@ def batched(args, local):
 
     for name, mode, inner in (("f32_refined", sip.SIP_MODE_F32_REFINED, args.inner), ("f64", sip.SIP_MODE_F64, 1)):
         ifs = [sip.sip_interface(lo, hi, nj, nk) for lo, hi, nj, nk in mesh.ifaces]
-        plan = sip.Plan(ctx, descs, sip.default_options(mode=mode, inner_iters=inner, graphs=1), ifaces=ifs)
+        plan = sip.Plan(ctx, descs, sip.default_options(mode=mode, inner_iters=inner, graphs=1, autotune=1),
+                        ifaces=ifs)
         zero()
         plan.iterate(2)
         zero()
@@ -629,6 +631,7 @@ def batched(args, local):
         e1.record(stream)
         torch.cuda.synchronize()
         out[name] = {"value": round(mesh.n * args.batched_iters * inner / (ms / 1e3) / 1e6, 1), "unit": "MLUP/s",
+                     "tile": dict(zip(("rows_per_thread", "tile_k", "stages"), plan.shape())),
                      "ms_per_iteration": round(ms / args.batched_iters, 3),
                      "time_to_1e-8": {"seconds": round(e0.elapsed_time(e1) / 1e3, 3), "iterations": it,
                                       "sip_iterations": it * inner, "relres": rel, "converged": bool(conv)}}

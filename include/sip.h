@@ -114,6 +114,13 @@ typedef struct {
                               non-NULL stream, ignored while profiling); 0: launch by launch */
   int32_t rows_per_thread; /* rows of a column tile each sweep thread walks (the tile is
                               32 x rows_per_thread * warps): 0 (auto), 2 or 4 */
+  int32_t autotune;        /* 1 (with tile_k, rows_per_thread and stages all 0): sip_factor builds
+                              the cost model's best few tile shapes, times their forward +
+                              backward sweeps on the plan's own work vectors and keeps the
+                              fastest plan; with the environment variable SIP_AUTOTUNE_CACHE
+                              naming a file, a result for the same signature (GPU SM count,
+                              mode, symmetry, coefficient type, block sizes) is read from it
+                              and new results are appended.  0: the cost model alone. */
 } sip_options;
 
 /* Fills *opt with defaults: alpha 0.92, SIP_MODE_F64, inner_iters 4. Host pointer. */
@@ -242,6 +249,9 @@ const char *sip_kernel_name(int kind);
 
 /* Total device bytes owned by the plan (host out). */
 int sip_plan_bytes(sip_plan *plan, size_t *bytes_out);
+/* The plan's tile shape: rows per thread, tile height (tile_k) and stage
+ * depth of its forward sweep (host pointers, each may be NULL). */
+int sip_plan_shape(sip_plan *plan, int *rows_per_thread, int *tile_k, int *stages);
 int sip_plan_destroy(sip_plan *plan);
 
 #ifdef __cplusplus

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -502,10 +503,11 @@ struct ShapeChoice {
   double score = 1e300;
 };
 
-ShapeChoice choose_shape(sip_ctx *ctx, const std::vector<BlockHost> &blocks, const std::vector<int> &kinds,
-                         int tab_ints, int forceTK, int forceR, int forceQ, bool fp64) {
+std::vector<ShapeChoice> shape_candidates(sip_ctx *ctx, const std::vector<BlockHost> &blocks,
+                                          const std::vector<int> &kinds, int tab_ints, int forceTK, int forceR,
+                                          int forceQ, bool fp64) {
   const double beta = fp64 ? 0.057 : 0.04;
-  ShapeChoice best;
+  std::vector<ShapeChoice> all;
   for (int Q : kQs)
     for (int NW = 1; NW <= 16; ++NW) {
       const int TK = Q * NW, NT = 32 * NW;
@@ -550,9 +552,115 @@ ShapeChoice choose_shape(sip_ctx *ctx, const std::vector<BlockHost> &blocks, con
       const double per_sm = (double)NW * std::max(1, (c.ntiles + ctx->nsm - 1) / ctx->nsm);
       // four rows per thread: measured 1.45x the step time of two at equal TK
       c.score = (double)steps * (1.0 + beta * per_sm) * (Q == 4 ? 1.45 : 1.0) * waves * (waves > 1 ? 4.0 : 1.0);
-      if (c.score < best.score) best = c;
+      all.push_back(c);
     }
-  return best;
+  std::stable_sort(all.begin(), all.end(), [](const ShapeChoice &a, const ShapeChoice &b) { return a.score < b.score; });
+  return all;
+}
+
+ShapeChoice choose_shape(sip_ctx *ctx, const std::vector<BlockHost> &blocks, const std::vector<int> &kinds,
+                         int tab_ints, int forceTK, int forceR, int forceQ, bool fp64) {
+  const std::vector<ShapeChoice> c = shape_candidates(ctx, blocks, kinds, tab_ints, forceTK, forceR, forceQ, fp64);
+  return c.empty() ? ShapeChoice() : c.front();
+}
+
+// ------------------------------------------------------------ autotuner
+// sip_options.autotune: the cost model's best few shapes are built as plans
+// and their forward + backward sweeps timed on the plan's own buffers; the
+// fastest plan is kept.  With SIP_AUTOTUNE_CACHE naming a file, results are
+// read from and appended to it, one line per problem signature:
+//   <signature> <rows_per_thread> <tile_k> <stages> <ms per sweep pair>
+constexpr int kTuneCandidates = 3;
+constexpr int kTuneReps = 3;
+std::mutex g_tune_mu;
+
+std::string tune_signature(const sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const sip_options &o) {
+  std::string dims;
+  for (int b = 0; b < nblocks; ++b)
+    dims += std::to_string(blocks[b].nx) + "x" + std::to_string(blocks[b].ny) + "x" + std::to_string(blocks[b].nz) + ",";
+  if (nblocks > 4) {  // long lists: FNV-1a of the dims
+    unsigned long long h = 1469598103934665603ull;
+    for (unsigned char ch : dims) h = (h ^ ch) * 1099511628211ull;
+    char buf[32];
+    std::snprintf(buf, sizeof(buf), "h%016llx", h);
+    dims = buf;
+  }
+  return "sm" + std::to_string(ctx->nsm) + "/m" + std::to_string(o.mode) + "/s" + std::to_string(blocks[0].symmetric) +
+         "/c" + std::to_string(blocks[0].coef_dtype) + "/b" + std::to_string(nblocks) + "/" + dims;
+}
+
+bool tune_lookup(const std::string &sig, int &Q, int &TK, int &R) {
+  const char *path = getenv("SIP_AUTOTUNE_CACHE");
+  if (!path || !*path) return false;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  FILE *f = fopen(path, "r");
+  if (!f) return false;
+  char line[4096];
+  bool found = false;
+  while (fgets(line, sizeof(line), f)) {  // the last entry of a signature wins
+    char key[4096];
+    int q = 0, tk = 0, r = 0;
+    double ms = 0;
+    if (line[0] == '#' || sscanf(line, "%4095s %d %d %d %lf", key, &q, &tk, &r, &ms) < 4) continue;
+    if (sig == key) {
+      Q = q;
+      TK = tk;
+      R = r;
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+void tune_store(const std::string &sig, int Q, int TK, int R, double ms) {
+  const char *path = getenv("SIP_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  FILE *f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d %d %d %.4f\n", sig.c_str(), Q, TK, R, ms);
+  fclose(f);
+}
+
+// ms per forward + backward sweep pair of a built plan, on its own work
+// vectors (zeroed first; the caller's x is not touched).
+double time_sweeps(sip_plan *p) {
+  sip_ctx *ctx = p->ctx;
+  cudaStream_t st = ctx->stream;
+  const bool f64 = p->mode == SIP_MODE_F64;
+  if (f64) {
+    if (cudaMemsetAsync(p->y64, 0, (size_t)p->ncells * 8, st) != cudaSuccess) return -1;
+  } else if (cudaMemsetAsync(p->y32, 0, (size_t)p->ncells * 4, st) != cudaSuccess ||
+             cudaMemsetAsync(p->d32, 0, (size_t)p->ncells * 4, st) != cudaSuccess) {
+    return -1;
+  }
+  if (cudaMemsetAsync(p->x64, 0, (size_t)p->ncells * 8, st) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(p->tickets, 0, 4 * sizeof(int), st) != cudaSuccess) return -1;
+  if (launch_set_ctl(p->ctl, -1.0, 0, st) != cudaSuccess) return -1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double ms = -1;
+  bool ok = true;
+  for (int r = 0; r <= kTuneReps && ok; ++r) {  // the first pair warms up
+    if (r == 1) cudaEventRecord(e0, st);
+    if (f64) {
+      ok = enqueue_forward(p, K_FWD64, (const double *)p->y64, p->y64) == SIP_OK &&
+           enqueue_backward(p, K_BWD64, (const double *)p->y64, p->x64) == SIP_OK;
+    } else {
+      ok = enqueue_forward(p, K_FWD32, (const float *)p->y32, p->y32) == SIP_OK &&
+           enqueue_backward(p, K_BWD32, (const float *)p->y32, p->d32) == SIP_OK;
+    }
+  }
+  cudaEventRecord(e1, st);
+  float t = 0.f;
+  if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
+    ms = t / kTuneReps;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (check_status(p) != SIP_OK) ms = -1;
+  return ms;
 }
 
 }  // namespace
@@ -675,6 +783,55 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     return fail(ctx, SIP_ERR_INVALID_ARG, "stages must be 0 (auto), 4 or 6");
   if (opt.rows_per_thread != 0 && opt.rows_per_thread != 2 && opt.rows_per_thread != 4)
     return fail(ctx, SIP_ERR_INVALID_ARG, "rows_per_thread must be 0 (auto), 2 or 4");
+  if (opt.autotune != 0 && opt.autotune != 1) return fail(ctx, SIP_ERR_INVALID_ARG, "autotune must be 0 or 1");
+  if (opt.autotune && opt.tile_k == 0 && opt.rows_per_thread == 0 && opt.stages == 0) {
+    const std::string sig = tune_signature(ctx, blocks, nblocks, opt);
+    sip_options o = opt;
+    o.autotune = 0;
+    o.tile_j = kTJ;
+    if (tune_lookup(sig, o.rows_per_thread, o.tile_k, o.stages)) {
+      const int rc = sip_factor(ctx, blocks, nblocks, ifaces, nifaces, &o, out);
+      if (rc == SIP_OK) return rc;  // a stale entry (another build's shapes) falls through to tuning
+    }
+    // candidates from the cost model
+    std::vector<BlockHost> bh(nblocks);
+    int tab_ints = 0;
+    for (int b = 0; b < nblocks; ++b) {
+      bh[b].d = blocks[b];
+      tab_ints = std::max(tab_ints, (blocks[b].nx + blocks[b].ny + blocks[b].nz - 2) + (blocks[b].nx + blocks[b].ny - 1));
+    }
+    const std::vector<ShapeChoice> cand =
+        shape_candidates(ctx, bh, plan_kinds(opt.mode), tab_ints, 0, 0, 0, opt.mode == SIP_MODE_F64);
+    sip_plan *best = nullptr;
+    double best_ms = 0;
+    int tried = 0, last_rc = SIP_OK;  // candidates built and timed
+    for (const ShapeChoice &c : cand) {
+      if (tried == kTuneCandidates) break;
+      o.rows_per_thread = c.Q;
+      o.tile_k = c.Q * c.NW;
+      o.stages = c.R[plan_kinds(opt.mode)[1]];
+      sip_plan *tp = nullptr;
+      last_rc = sip_factor(ctx, blocks, nblocks, ifaces, nifaces, &o, &tp);
+      if (last_rc != SIP_OK) {
+        if (best) break;  // e.g. no room for a second plan next to the best one: keep the best
+        return last_rc;   // breakdown or invalid input: no shape changes that
+      }
+      ++tried;
+      const double ms = time_sweeps(tp);
+      if (ms > 0 && (!best || ms < best_ms)) {
+        if (best) sip_plan_destroy(best);
+        best = tp;
+        best_ms = ms;
+      } else {
+        sip_plan_destroy(tp);
+      }
+    }
+    if (!best) return fail(ctx, SIP_ERR_CUDA, "autotune: no candidate shape could be timed");
+    tune_store(sig, best->Q, best->TK, best->Rk[plan_kinds(opt.mode)[1]], best_ms);
+    best->opt.autotune = 1;
+    *out = best;
+    return SIP_OK;
+  }
 
   sip_plan *p = new sip_plan();
   p->ctx = ctx;
@@ -1178,6 +1335,14 @@ const char *sip_kernel_name(int kind) {
   static_assert(sizeof(names) / sizeof(names[0]) == K_NKINDS + 1, "kernel names");
   if (kind < 0 || kind > K_NKINDS) return nullptr;
   return names[kind];
+}
+
+int sip_plan_shape(sip_plan *p, int *rows_per_thread, int *tile_k, int *stages) {
+  if (!p) return SIP_ERR_INVALID_ARG;
+  if (rows_per_thread) *rows_per_thread = p->Q;
+  if (tile_k) *tile_k = p->TK;
+  if (stages) *stages = p->Rk[plan_kinds(p->mode)[1]];
+  return SIP_OK;
 }
 
 int sip_plan_bytes(sip_plan *p, size_t *bytes_out) {

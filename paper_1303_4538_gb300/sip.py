@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from typing import List, Optional, Sequence
+from typing import List, Optional, Sequence, Tuple
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsip.so")
@@ -40,7 +40,7 @@ ERROR_NAMES = {
 # every symbol include/sip.h declares
 EXPORTED = (
     "sip_default_options", "sip_create", "sip_destroy", "sip_last_error", "sip_factor",
-    "sip_iterate", "sip_solve", "sip_get_history", "sip_export_factors", "sip_plan_bytes",
+    "sip_iterate", "sip_solve", "sip_get_history", "sip_export_factors", "sip_plan_bytes", "sip_plan_shape",
     "sip_plan_destroy", "sip_plane_layout", "sip_profile_enable", "sip_profile_read",
     "sip_launch_count", "sip_kernel_name", "sip_residual_norm",
     "sip_residual_norm_noalloc", "sip_server_start", "sip_server_submit", "sip_server_poll", "sip_server_stop",
@@ -69,7 +69,7 @@ class sip_options(ctypes.Structure):
         ("alpha", ctypes.c_double), ("mode", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
         ("max_spin", ctypes.c_int64), ("tile_j", ctypes.c_int32), ("tile_k", ctypes.c_int32),
         ("stages", ctypes.c_int32), ("debug_stall", ctypes.c_int32), ("graphs", ctypes.c_int32),
-        ("rows_per_thread", ctypes.c_int32),
+        ("rows_per_thread", ctypes.c_int32), ("autotune", ctypes.c_int32),
     ]
 
 
@@ -105,6 +105,7 @@ def lib():
         L.sip_get_history.argtypes = [P, ctypes.POINTER(D), I, ctypes.POINTER(I)]
         L.sip_export_factors.argtypes = [P, I, ctypes.POINTER(P)]
         L.sip_plan_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        L.sip_plan_shape.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
         L.sip_plan_destroy.argtypes = [P]
         L.sip_plane_layout.argtypes = [I, I, I, P]
         L.sip_profile_enable.argtypes = [P, I]
@@ -253,6 +254,12 @@ class Plan:
         b = ctypes.c_size_t(0)
         self.ctx.check(lib().sip_plan_bytes(self.h, ctypes.byref(b)))
         return b.value
+
+    def shape(self) -> Tuple[int, int, int]:
+        """(rows_per_thread, tile_k, stages) of the plan's sweeps."""
+        q, tk, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self.ctx.check(lib().sip_plan_shape(self.h, ctypes.byref(q), ctypes.byref(tk), ctypes.byref(r)))
+        return q.value, tk.value, r.value
 
     def close(self):
         if self.h:

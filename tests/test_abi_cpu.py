@@ -40,9 +40,9 @@ def test_struct_layout_matches_header(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(sip_block_desc), offsetof(sip_block_desc, ap),
          offsetof(sip_block_desc, b), offsetof(sip_block_desc, x), offsetof(sip_block_desc, symmetric));
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(sip_options), offsetof(sip_options, max_spin),
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(sip_options), offsetof(sip_options, max_spin),
          offsetof(sip_options, tile_j), offsetof(sip_options, debug_stall), offsetof(sip_options, graphs),
-         offsetof(sip_options, rows_per_thread));
+         offsetof(sip_options, rows_per_thread), offsetof(sip_options, autotune));
   printf("%zu\n", sizeof(sip_interface));
   return 0;
 }
@@ -54,7 +54,7 @@ int main(void) {
     D, O, I = sip.sip_block_desc, sip.sip_options, sip.sip_interface
     want = [ctypes.sizeof(D), D.ap.offset, D.b.offset, D.x.offset, D.symmetric.offset,
             ctypes.sizeof(O), O.max_spin.offset, O.tile_j.offset, O.debug_stall.offset, O.graphs.offset,
-            O.rows_per_thread.offset, ctypes.sizeof(I)]
+            O.rows_per_thread.offset, O.autotune.offset, ctypes.sizeof(I)]
     assert got == want
 
 
