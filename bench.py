@@ -718,6 +718,7 @@ def serving(args, local):
                 lat[k] = fin[k] - arr[k]
                 bad += res[0] != sip.SIP_OK
         time.sleep(0.0002)
+    sst = srv.stats()
     srv.stop()
     ctx.close()
     ms = lambda v, q: round(float(np.percentile(np.array(v) * 1e3, q)), 3)
@@ -726,7 +727,9 @@ def serving(args, local):
                                                         "slots": args.serve_slots,
                                                         "solves_per_s": round(N / (max(fin) - arr[0]), 2),
                                                         "p50_ms": ms(lat, 50), "p99_ms": ms(lat, 99),
-                                                        "failed": int(bad)},
+                                                        "failed": int(bad),
+                                                        "peak_admitted_bytes": int(sst["peak_in_use_bytes"]),
+                                                        "slot_busy_s": round(sst["busy_ms"] / 1e3, 3)},
             "serial_fp64": {"solves_per_s": round(cap, 2), "p50_ms": ms(lat_ser, 50), "p99_ms": ms(lat_ser, 99)}}
 
 

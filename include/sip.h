@@ -234,6 +234,21 @@ int sip_server_poll(sip_server *srv, uint64_t ticket, int *done, int *status, in
 /* Stops accepting requests, runs the queued ones to completion, joins the
  * slots and frees the server. */
 int sip_server_stop(sip_server *srv);
+/* Counters and state of a server (a snapshot; host struct).  The watchdog
+ * field: oldest_running_ms is the age of the longest-running admitted
+ * request (0 when none runs), for a caller to act on a stuck or runaway
+ * solve (every device wait of a solve is bounded, so a solve always ends;
+ * this measures how long it has taken so far). */
+typedef struct {
+  uint64_t submitted, completed, failed; /* requests; failed: done with a status other than SIP_OK */
+  uint32_t queued, running;              /* waiting for admission / on a slot now */
+  uint32_t slots;
+  size_t budget_bytes, in_use_bytes;     /* HBM budget and the admitted requests' estimated footprint */
+  size_t peak_in_use_bytes;
+  double oldest_running_ms;
+  double busy_ms;                        /* summed wall time of finished requests on their slots */
+} sip_server_stats;
+int sip_server_get_stats(sip_server *srv, sip_server_stats *out);
 
 /* Measurement aids.  sip_profile_enable(plan, 1) records a CUDA event pair
  * on the plan's stream around every later kernel launch of the plan;

@@ -14,8 +14,10 @@
 // another.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <mutex>
 #include <string>
@@ -60,7 +62,11 @@ size_t estimate_footprint(const sip_block_desc &d, const sip_options &o) {
 
 struct sip_server {
   int device = 0;
-  size_t budget = 0, in_use = 0;
+  size_t budget = 0, in_use = 0, peak_in_use = 0;
+  uint64_t submitted = 0, completed = 0, failed = 0;
+  double busy_ms = 0;
+  std::vector<std::chrono::steady_clock::time_point> started;  // per slot: admission of its request
+  std::vector<char> running;                                    // per slot: a request is on it
   int max_slots = 0;
   size_t queue_cap = 4096;
   uint64_t next_ticket = 1;
@@ -80,7 +86,6 @@ void slot_loop(sip_server *s, int slot) {
   sip_ctx *ctx = nullptr;
   const bool ok = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess &&
                   sip_create(&ctx, s->device, stream) == SIP_OK;
-  (void)slot;
   for (;;) {
     Request r{};
     r.ticket = 0;
@@ -95,6 +100,9 @@ void slot_loop(sip_server *s, int slot) {
             r = *it;
             s->queue.erase(it);
             s->in_use += r.footprint;
+            s->peak_in_use = std::max(s->peak_in_use, s->in_use);
+            s->running[slot] = 1;
+            s->started[slot] = std::chrono::steady_clock::now();
             return true;
           }
           break;  // arrival order: later requests wait behind the oldest
@@ -122,6 +130,10 @@ void slot_loop(sip_server *s, int slot) {
       std::lock_guard<std::mutex> lk(s->mu);
       s->in_use -= r.footprint;
       s->results[r.ticket] = res;
+      s->running[slot] = 0;
+      s->completed += 1;
+      s->failed += res.status != SIP_OK;
+      s->busy_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - s->started[slot]).count();
     }
     s->cv.notify_all();
   }
@@ -142,6 +154,8 @@ int sip_server_start(sip_ctx *ctx, size_t hbm_budget_bytes, int max_slots, sip_s
   s->device = dev;
   s->budget = hbm_budget_bytes;
   s->max_slots = max_slots;
+  s->started.assign(max_slots, std::chrono::steady_clock::time_point());
+  s->running.assign(max_slots, 0);
   for (int q = 0; q < max_slots; ++q) s->workers.emplace_back(slot_loop, s, q);
   *out = s;
   return SIP_OK;
@@ -163,6 +177,7 @@ int sip_server_submit(sip_server *s, const sip_block_desc *blk, const sip_option
     if (s->queue.size() >= s->queue_cap) return SIP_ERR_BUSY;
     r.ticket = s->next_ticket++;
     s->queue.push_back(r);
+    s->submitted += 1;
     s->results[r.ticket] = Result();
     *ticket = r.ticket;
   }
@@ -181,6 +196,29 @@ int sip_server_poll(sip_server *s, uint64_t ticket, int *done, int *status, int 
   if (iters) *iters = r.iters;
   if (relres) *relres = r.relres;
   if (r.done) s->results.erase(it);  // a finished ticket is reported once
+  return SIP_OK;
+}
+
+int sip_server_get_stats(sip_server *s, sip_server_stats *out) {
+  if (!s || !out) return SIP_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  std::memset(out, 0, sizeof(*out));
+  out->submitted = s->submitted;
+  out->completed = s->completed;
+  out->failed = s->failed;
+  out->queued = (uint32_t)s->queue.size();
+  out->slots = (uint32_t)s->max_slots;
+  out->budget_bytes = s->budget;
+  out->in_use_bytes = s->in_use;
+  out->peak_in_use_bytes = s->peak_in_use;
+  out->busy_ms = s->busy_ms;
+  const auto now = std::chrono::steady_clock::now();
+  for (int q = 0; q < s->max_slots; ++q)
+    if (s->running[q]) {
+      out->running += 1;
+      out->oldest_running_ms =
+          std::max(out->oldest_running_ms, std::chrono::duration<double, std::milli>(now - s->started[q]).count());
+    }
   return SIP_OK;
 }
 

@@ -44,6 +44,7 @@ EXPORTED = (
     "sip_plan_destroy", "sip_plane_layout", "sip_profile_enable", "sip_profile_read",
     "sip_launch_count", "sip_kernel_name", "sip_residual_norm",
     "sip_residual_norm_noalloc", "sip_server_start", "sip_server_submit", "sip_server_poll", "sip_server_stop",
+    "sip_server_get_stats",
 )
 
 
@@ -56,6 +57,15 @@ class sip_block_desc(ctypes.Structure):
         ("at", ctypes.c_void_p),
         ("b", ctypes.c_void_p), ("x", ctypes.c_void_p),
         ("symmetric", ctypes.c_int32),
+    ]
+
+
+class sip_server_stats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+        ("queued", ctypes.c_uint32), ("running", ctypes.c_uint32), ("slots", ctypes.c_uint32),
+        ("budget_bytes", ctypes.c_size_t), ("in_use_bytes", ctypes.c_size_t), ("peak_in_use_bytes", ctypes.c_size_t),
+        ("oldest_running_ms", ctypes.c_double), ("busy_ms", ctypes.c_double),
     ]
 
 
@@ -120,6 +130,7 @@ def lib():
         L.sip_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                       ctypes.POINTER(D)]
         L.sip_server_stop.argtypes = [P]
+        L.sip_server_get_stats.argtypes = [P, ctypes.c_void_p]
         L.sip_kernel_name.restype = ctypes.c_char_p
         for name in EXPORTED:
             if name not in ("sip_default_options", "sip_last_error", "sip_kernel_name"):
@@ -319,6 +330,14 @@ class Server:
             return None
         self._keep.pop(ticket, None)
         return st.value, it.value, rel.value
+
+    def stats(self) -> dict:
+        """sip_server_get_stats as a dict."""
+        st = sip_server_stats()
+        rc = lib().sip_server_get_stats(self.h, ctypes.byref(st))
+        if rc != SIP_OK:
+            raise SipError(rc, "sip_server_get_stats failed")
+        return {name: getattr(st, name) for name, _ in st._fields_}
 
     def stop(self):
         if self.h:

@@ -44,6 +44,8 @@ int main(void) {
          offsetof(sip_options, tile_j), offsetof(sip_options, debug_stall), offsetof(sip_options, graphs),
          offsetof(sip_options, rows_per_thread), offsetof(sip_options, autotune));
   printf("%zu\n", sizeof(sip_interface));
+  printf("%zu %zu %zu %zu\n", sizeof(sip_server_stats), offsetof(sip_server_stats, queued),
+         offsetof(sip_server_stats, budget_bytes), offsetof(sip_server_stats, oldest_running_ms));
   return 0;
 }
 ''')
@@ -55,6 +57,8 @@ int main(void) {
     want = [ctypes.sizeof(D), D.ap.offset, D.b.offset, D.x.offset, D.symmetric.offset,
             ctypes.sizeof(O), O.max_spin.offset, O.tile_j.offset, O.debug_stall.offset, O.graphs.offset,
             O.rows_per_thread.offset, O.autotune.offset, ctypes.sizeof(I)]
+    S = sip.sip_server_stats
+    want += [ctypes.sizeof(S), S.queued.offset, S.budget_bytes.offset, S.oldest_running_ms.offset]
     assert got == want
 
 

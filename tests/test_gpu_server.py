@@ -36,7 +36,12 @@ def _serve(torch, reqs, budget, slots):
     out = {}
     polled_twice = None
     t0 = time.time()
+    seen = {"running": 0, "watch": True}
     while len(out) < len(tickets) and time.time() - t0 < 300:
+        st = srv.stats()   # the counters and the watchdog age stay consistent while requests run
+        seen["running"] = max(seen["running"], st["running"])
+        seen["watch"] &= (st["oldest_running_ms"] > 0) == (st["running"] > 0)
+        assert st["running"] <= slots and st["submitted"] == len(tickets)
         for t in tickets:
             if t not in out:
                 res = srv.poll(t)
@@ -47,9 +52,13 @@ def _serve(torch, reqs, budget, slots):
                             srv.poll(t)
                         polled_twice = e.value.code
         time.sleep(0.001)
+    st = srv.stats()
+    assert st["completed"] == len(tickets) and st["failed"] == 0 and st["queued"] == 0 and st["running"] == 0
+    assert st["budget_bytes"] == budget and st["in_use_bytes"] == 0 and st["busy_ms"] > 0
+    assert seen["watch"]
     srv.stop()
     assert len(out) == len(tickets) and polled_twice == sip.SIP_ERR_NOT_FOUND
-    return [out[t] for t in tickets], ctx
+    return [out[t] for t in tickets], ctx, seen["running"], st
 
 
 def _alone(torch, ctx, r):
@@ -66,7 +75,9 @@ def test_results_equal_alone_and_in_the_mix():
     torch = torch_cuda()
     rng = np.random.default_rng(101)
     reqs = [_request(torch, q, rng) for q in range(12)]
-    res, ctx = _serve(torch, reqs, 64 << 30, 4)
+    res, ctx, running, st = _serve(torch, reqs, 64 << 30, 4)
+    assert running >= 2   # requests overlapped on the device
+    assert st["peak_in_use_bytes"] <= 64 << 30
     for r, (status, it, rel) in zip(reqs, res):
         assert status in (sip.SIP_OK, sip.SIP_NOT_CONVERGED)
         assert status == sip.SIP_OK and rel <= r["rtol"]
@@ -80,7 +91,8 @@ def test_small_budget_admits_one_at_a_time():
     torch = torch_cuda()
     rng = np.random.default_rng(102)
     reqs = [_request(torch, q, rng) for q in range(5)]
-    res, ctx = _serve(torch, reqs, 1 << 20, 3)   # every request exceeds the budget: they run alone, in order
+    res, ctx, running, st = _serve(torch, reqs, 1 << 20, 3)   # every request exceeds the budget: alone, in order
+    assert running == 1
     for r, (status, it, rel) in zip(reqs, res):
         assert status == sip.SIP_OK and rel <= r["rtol"]
         it1, rel1, x1 = _alone(torch, ctx, r)
