@@ -544,6 +544,7 @@ std::vector<ShapeChoice> shape_candidates(sip_ctx *ctx, const std::vector<BlockH
         const int nTJ = (bh.d.ny + kTJ - 1) / kTJ, nTK = (bh.d.nz + TK - 1) / TK;
         c.ntiles += nTJ * nTK;
         const int R = c.R[kinds[1]];
+        // hop slack of the fitted model (the per-step factor beta was fitted with it)
         const int lead = std::min(R + 1, std::max(bh.d.nx - 1, 0));
         steps = std::max(steps, (long long)(nTJ - 1) * (kTJ + lead) + (long long)(nTK - 1) * (TK + lead) +
                                     bh.d.nx + kTJ + TK - 2);
