@@ -106,7 +106,7 @@ typedef struct {
   int32_t inner_iters;     /* SIP_MODE_F32_REFINED: FP32 iterations per FP64 correction (>= 1) */
   int64_t max_spin;        /* polls before a device wait gives up (<= 0: default 2^22) */
   int32_t tile_j, tile_k;  /* column-tile shape of the sweeps (0: chosen by the autotuner) */
-  int32_t stages;          /* depth of the sweeps' shared-memory prefetch ring: 0 (auto), 4 or 6 */
+  int32_t stages;          /* depth of the sweeps' shared-memory prefetch ring: 0 (auto), 3, 4 or 6 */
   int32_t debug_stall;     /* test hook: 1 makes the sweeps wait for a tag no producer
                               writes, so the bounded waits time out (SIP_ERR_DEVICE_TIMEOUT) */
   int32_t graphs;          /* 1: queue iterations by replaying CUDA graphs captured on the

@@ -495,8 +495,9 @@ std::vector<int> plan_kinds(int mode) {
 // Poisson blocks, every shape) as 1 + beta x warps per SM with beta = 0.04
 // for the FP32 sweeps and 0.057 for FP64, and 1.45x longer with four rows per
 // thread than with two at the same TK.  Only shapes whose tiles are all
-// resident at once are taken (else the fewest waves); R = 4 unless forced
-// (a deeper ring measured slower: more start slack, more stale faces).
+// resident at once are taken (else the fewest waves); R = 3 unless forced
+// (deeper rings measured slower on GB300: 3 beat 4 by up to 11 % and 6 is
+// slower still).
 struct ShapeChoice {
   int Q = 0, NW = 0, ntiles = 0;
   int R[K_NKINDS] = {}, cap[K_NKINDS] = {};
@@ -522,7 +523,7 @@ std::vector<ShapeChoice> shape_candidates(sip_ctx *ctx, const std::vector<BlockH
       for (int kind : kinds) {
         const bool fac = kind == K_FACTOR || kind == K_FACTOR32;
         int bR = 0, bcap = 0;
-        for (int R : {4, 6, 2}) {
+        for (int R : {3, 4, 6, 2}) {
           // the one-off factorisation may drop to a 2-stage ring when its
           // 64-byte input records do not fit a wide tile
           if (R == 2 ? !fac : (forceR > 0 && R != forceR)) continue;
@@ -531,7 +532,7 @@ std::vector<ShapeChoice> shape_candidates(sip_ctx *ctx, const std::vector<BlockH
           if (smem + ctx->kernel_static_smem > ctx->smem_optin) continue;
           const int capk = ctx->nsm * max_active(kernel_ptr(kind, Q, R), NT, smem);
           if (capk > bcap) { bR = R; bcap = capk; }
-          if (forceR == 0 && capk > 0 && R == 4) break;  // R = 4 when it fits
+          if (forceR == 0 && capk > 0 && R == 3) break;  // R = 3 when it fits
         }
         if (bcap < 1) { ok = false; break; }
         c.R[kind] = bR;
@@ -780,8 +781,8 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
   if (opt.tile_j != 0 && opt.tile_j != kTJ) return fail(ctx, SIP_ERR_INVALID_ARG, "tile_j must be 0 or 32");
   if (opt.tile_k < 0 || opt.tile_k > 64 || (opt.tile_k > 0 && opt.tile_k % 2 != 0))
     return fail(ctx, SIP_ERR_INVALID_ARG, "tile_k must be 0 (auto) or an even number <= 64");
-  if (opt.stages != 0 && opt.stages != 4 && opt.stages != 6)
-    return fail(ctx, SIP_ERR_INVALID_ARG, "stages must be 0 (auto), 4 or 6");
+  if (opt.stages != 0 && opt.stages != 3 && opt.stages != 4 && opt.stages != 6)
+    return fail(ctx, SIP_ERR_INVALID_ARG, "stages must be 0 (auto), 3, 4 or 6");
   if (opt.rows_per_thread != 0 && opt.rows_per_thread != 2 && opt.rows_per_thread != 4)
     return fail(ctx, SIP_ERR_INVALID_ARG, "rows_per_thread must be 0 (auto), 2 or 4");
   if (opt.autotune != 0 && opt.autotune != 1) return fail(ctx, SIP_ERR_INVALID_ARG, "autotune must be 0 or 1");

@@ -25,7 +25,7 @@ enum KernelKind {
 };
 
 constexpr int kQs[2] = {2, 4};
-constexpr int kRs[3] = {2, 4, 6};  // 2: the factorisation only (wide tiles)
+constexpr int kRs[4] = {2, 3, 4, 6};  // 2: the factorisation only (wide tiles)
 
 // sweep kernel of a kind (nullptr for the row kinds)
 const void *kernel_ptr(int kind, int Q, int R);

@@ -45,6 +45,8 @@ class GpuSystem:
             opts.tile_j, opts.tile_k = tile[:2]
             if len(tile) > 2:
                 opts.rows_per_thread = tile[2]
+            if len(tile) > 3:
+                opts.stages = tile[3]
         torch.cuda.synchronize()
         ifs = None
         if ifaces:
