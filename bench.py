@@ -439,6 +439,7 @@ def run_gb300(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"poisson_{args.n}cube", "cells": N, "alpha": 0.92, "mode": "f32_refined",
                    "inner_iters": args.inner, "max_corrections_per_step": args.iters, "rtol": 1e-8,
+                   "tile": dict(zip(("rows_per_thread", "tile_k", "stages"), plan_r.shape())),
                    "parallelism": f"replicas x{world}", "l2": "working set > L2 (plan arrays "
                    f"{plan_r.nbytes() / 1e9:.2f} GB)", "step": "sip_solve on the factored plan, x reset to 0"},
         "roofline": roofline(prof_r),
