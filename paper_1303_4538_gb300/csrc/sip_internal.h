@@ -57,11 +57,12 @@ __host__ __device__ inline int plane_row_base(const int *PO, const int *F, int m
 }
 
 // Steps a substitution sweep's tile lets its upstream tiles run ahead before
-// it starts (the start slack).  A tile's first prefetched faces may then be
-// stale and are re-read, which costs less than the longer pipeline fill of a
-// larger slack (measured on GB300 with a 4-stage ring: 2 steps 6 % faster
-// than 5 at 256^3, 13 % at 128^3; 0..3 steps within 4 %).
-__host__ __device__ constexpr int sweep_lead(int) { return 2; }
+// it starts (the start slack), by value size.  A tile's first prefetched
+// faces may then be stale and are re-read, which costs less than the longer
+// pipeline fill of a larger slack (measured on GB300: 2 steps 6 % faster than
+// 5 at 256^3, 13 % at 128^3; with the 3-stage ring 1 step is best for FP32,
+// 2 for FP64, within 4 % of each other).
+__host__ __device__ constexpr int sweep_lead(int esize) { return esize == 4 ? 1 : 2; }
 
 struct Tile {
   int blk;    // block index

@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
     uint64_t *upJ = g.hasS ? tile_faces(c, B, tl.gtile - 1) : myf;
     uint64_t *upK = g.hasB ? tile_faces(c, B, tl.gtile - B.nTJ) : myf;
     {
-      const int lead = min(sweep_lead(R), B.nx - 1);
+      const int lead = min(sweep_lead((int)sizeof(T)), B.nx - 1);
       slack_gate<W>(g.hasS ? faceJ(upJ, B, lead + kTJ - 1, 0, W) : nullptr,
                     g.hasB ? faceK(upK, B, lead + TK - 1, 0, W) : nullptr, expect, c, abort, tr);
     }
@@ -789,7 +789,7 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
     {
       // the consumer of the last valid row (column) needs, `lead` steps into
       // the walk, cell i = nx-1-lead, published on the producer's step i + lane
-      const int lead = min(sweep_lead(R), B.nx - 1);
+      const int lead = min(sweep_lead((int)sizeof(T)), B.nx - 1);
       const int i = B.nx - 1 - lead;
       // (J records of row pairs sit in the slot of the pair's first row)
       slack_gate<W>(g.hasN ? faceJ(dnJ, B, i + g.nkt - 1, (g.nkt - 1) / PJ * PJ, W) : nullptr,
