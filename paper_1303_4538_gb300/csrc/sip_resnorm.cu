@@ -2,7 +2,7 @@
 // ||b - A x||_2 and ||b||_2 (the residual of resforward3d, arXiv:1303.4538
 // Sec. 4.1, evaluated directly on the caller's arrays instead of a plan's
 // plane layout).  Used to check a returned solution independently of the
-// sweeps' fused residual.
+// solver's own residual kernels.
 //
 // Two launches, both with a fixed summation order (bitwise reproducible):
 //   1. one CTA per chunk of kResChunk consecutive cells writes the pair

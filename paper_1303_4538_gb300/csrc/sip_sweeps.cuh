@@ -341,8 +341,8 @@ struct Vec {
 //   P1 = a (LB UN_B + LW UN_W),  P2 = a (LB UE_B + LS UE_S),  P3 = a (LW UT_W + LS UT_S),
 //   LP = AP + P1 + P2 + P3 - LB UT_B - LW UE_W - LS UN_S,
 //   UN = (AN - P1) / LP,  UE = (AE - P2) / LP,  UT = (AT - P3) / LP.
-// Arithmetic in FP64; stored (as TF) into the forward record [LB LW LS 1/LP]
-// and the backward record [UE UN UT 0].  Faces carry (UN, UE, UT): 48 bytes.
+// Arithmetic in FP64; stored (as TF) into the L record [LB LW LS 1/LP] and
+// the U record [UE UN UT 0].  Faces carry (UN, UE, UT): 48 bytes.
 template <typename TF, int Q, int R>
 __global__ void __launch_bounds__(512) k_factor(FacParams<TF> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
