@@ -515,6 +515,10 @@ std::vector<ShapeChoice> shape_candidates(sip_ctx *ctx, const std::vector<BlockH
       if (forceTK > 0 && TK != forceTK) continue;
       if (forceQ > 0 && Q != forceQ) continue;
       if (forceQ == 0 && forceTK == 0 && Q != 2) continue;  // 2 rows per thread measured fastest
+      // the model was fitted up to 8 warps per tile; 16 measured slower than
+      // it predicts (384^3 FP64: 32 x 32 tiles 5.85 ms per iteration, 32 x 24
+      // 4.85 ms), so automatic choices stop at 12
+      if (forceTK == 0 && NW > 12) continue;
       ShapeChoice c;
       c.Q = Q;
       c.NW = NW;
@@ -551,7 +555,8 @@ std::vector<ShapeChoice> shape_candidates(sip_ctx *ctx, const std::vector<BlockH
                                     bh.d.nx + kTJ + TK - 2);
       }
       const int waves = (c.ntiles + capmin - 1) / capmin;
-      const double per_sm = (double)NW * std::max(1, (c.ntiles + ctx->nsm - 1) / ctx->nsm);
+      // warps per SM, averaged: a few SMs holding a second tile cost a little
+      const double per_sm = (double)NW * std::max(1.0, (double)c.ntiles / ctx->nsm);
       // four rows per thread: measured 1.45x the step time of two at equal TK
       c.score = (double)steps * (1.0 + beta * per_sm) * (Q == 4 ? 1.45 : 1.0) * waves * (waves > 1 ? 4.0 : 1.0);
       all.push_back(c);
