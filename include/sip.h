@@ -128,8 +128,13 @@ void sip_default_options(sip_options *opt);
 
 /* Creates a context on CUDA device `device`, ordering all work on `stream`
  * (a cudaStream_t; NULL = legacy default stream).  *ctx (host) receives the
- * handle.  Errors: SIP_ERR_NO_DEVICE, SIP_ERR_INVALID_ARG. */
+ * handle.  The context's plans take device memory from its own
+ * stream-ordered pool (allocated and freed in `stream` order, up to 1 GiB
+ * kept cached between plans), so creating or destroying a plan does not
+ * synchronise the device.  Errors: SIP_ERR_NO_DEVICE, SIP_ERR_INVALID_ARG. */
 int sip_create(sip_ctx **ctx, int device, void *stream);
+/* Synchronises the stream and frees the context, its pool and cached pinned
+ * blocks.  Destroy the context's plans first. */
 int sip_destroy(sip_ctx *ctx);
 /* Description of the last error on ctx (never NULL; valid until the next
  * call on this thread).  ctx == NULL: the last sip_create failure. */
@@ -217,7 +222,9 @@ int sip_residual_norm_noalloc(sip_ctx *ctx, const sip_block_desc *blk, double *n
  * run concurrently, so requests arriving while others are on the GPU start as
  * soon as a slot and memory free up, and their kernels overlap.
  * The descriptor's arrays must stay valid (b and the coefficients unmodified)
- * until the request is done; the solution is written into blk->x. */
+ * until the request is done; the solution is written into blk->x.  Each slot
+ * has its own context, whose memory pool may keep up to 1 GiB cached beyond
+ * the admitted footprints. */
 typedef struct sip_server sip_server;
 /* Starts the slots.  ctx: a context on the device to use (its stream is not
  * used).  Errors: SIP_ERR_INVALID_ARG, SIP_ERR_NO_DEVICE. */

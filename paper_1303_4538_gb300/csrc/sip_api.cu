@@ -33,7 +33,18 @@ struct sip_ctx {
   size_t smem_optin = 0;
   std::string err = "no error";
   size_t kernel_static_smem = 0;  // largest static shared memory of any sweep kernel
+  // Device memory of the context's plans comes from its own stream-ordered
+  // pool (allocated and freed in stream order on `stream`): creating and
+  // destroying plans never synchronises the device, so the slots of a server
+  // admit and retire requests while other slots' kernels run.  Null: plain
+  // cudaMalloc / cudaFree.
+  cudaMemPool_t mempool = nullptr;
+  // pinned host control blocks of destroyed plans, reused by the next plans
+  std::mutex pin_mu;
+  std::vector<void *> pinned;
 };
+constexpr size_t kPinnedBlock = 256;  // 3 Ctl + 2 status words, rounded up
+constexpr unsigned long long kPoolKeep = 1ull << 30;  // bytes a context's pool keeps cached
 
 static std::string g_create_error = "no error";
 
@@ -146,11 +157,40 @@ struct sip_plan {
 // ------------------------------------------------------------------ helpers
 namespace {
 
+cudaError_t ctx_alloc(sip_ctx *ctx, void **v, size_t b) {
+  if (ctx->mempool) return cudaMallocFromPoolAsync(v, b, ctx->mempool, ctx->stream);
+  return cudaMalloc(v, b);
+}
+
+void ctx_free(sip_ctx *ctx, void *v) {
+  if (ctx->mempool) cudaFreeAsync(v, ctx->stream);
+  else cudaFree(v);
+}
+
+void *pinned_take(sip_ctx *ctx) {
+  {
+    std::lock_guard<std::mutex> lk(ctx->pin_mu);
+    if (!ctx->pinned.empty()) {
+      void *v = ctx->pinned.back();
+      ctx->pinned.pop_back();
+      return v;
+    }
+  }
+  void *v = nullptr;
+  return cudaMallocHost(&v, kPinnedBlock) == cudaSuccess ? v : nullptr;
+}
+
+void pinned_give(sip_ctx *ctx, void *v) {
+  if (!v) return;
+  std::lock_guard<std::mutex> lk(ctx->pin_mu);
+  ctx->pinned.push_back(v);
+}
+
 template <typename T>
 cudaError_t palloc(sip_plan *p, T **ptr, size_t count) {
   void *v = nullptr;
   const size_t b = std::max<size_t>(count, 1) * sizeof(T);
-  cudaError_t e = cudaMalloc(&v, b);
+  cudaError_t e = ctx_alloc(p->ctx, &v, b);
   if (e != cudaSuccess) return e;
   p->allocs.push_back(v);
   p->bytes += b;
@@ -163,7 +203,7 @@ void pfree(sip_plan *p, void *v, size_t bytes) {
   if (it != p->allocs.end()) {
     p->allocs.erase(it);
     p->bytes -= bytes;
-    cudaFree(v);
+    ctx_free(p->ctx, v);
   }
 }
 
@@ -178,10 +218,9 @@ void free_plan_memory(sip_plan *p) {
   p->recs.clear();
   for (auto e : p->pool) cudaEventDestroy(e);
   p->pool.clear();
-  for (void *v : p->allocs) cudaFree(v);
+  for (void *v : p->allocs) ctx_free(p->ctx, v);
   p->allocs.clear();
-  if (p->h_ctl) cudaFreeHost(p->h_ctl);
-  if (p->h_status) cudaFreeHost(p->h_status);
+  pinned_give(p->ctx, p->h_ctl);  // h_status lives in the same block
   p->h_ctl = nullptr;
   p->h_status = nullptr;
 }
@@ -704,6 +743,27 @@ int sip_create(sip_ctx **out, int device, void *stream) {
   }
   ctx->nsm = prop.multiProcessorCount;
   ctx->smem_optin = prop.sharedMemPerBlockOptin;
+  {
+    // the context's stream-ordered pool (falls back to cudaMalloc if the
+    // device or driver has none); keeps up to kPoolKeep bytes cached between
+    // plans instead of returning them at every synchronisation
+    int pools = 0;
+    cudaDeviceGetAttribute(&pools, cudaDevAttrMemoryPoolsSupported, device);
+    if (pools) {
+      cudaMemPoolProps props;
+      std::memset(&props, 0, sizeof(props));
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = device;
+      if (cudaMemPoolCreate(&ctx->mempool, &props) == cudaSuccess) {
+        unsigned long long keep = kPoolKeep;
+        cudaMemPoolSetAttribute(ctx->mempool, cudaMemPoolAttrReleaseThreshold, &keep);
+      } else {
+        ctx->mempool = nullptr;
+        cudaGetLastError();
+      }
+    }
+  }
   for (int kind = 0; kind < K_NKINDS; ++kind)
     for (int Q : kQs)
       for (int R : kRs) {
@@ -716,6 +776,7 @@ int sip_create(sip_ctx **out, int device, void *stream) {
                                    (int)(ctx->smem_optin - fa.sharedSizeBytes));
         if (e != cudaSuccess) {
           g_create_error = std::string("kernel attribute setup: ") + cudaGetErrorString(e);
+          if (ctx->mempool) cudaMemPoolDestroy(ctx->mempool);
           delete ctx;
           return SIP_ERR_CUDA;
         }
@@ -726,6 +787,11 @@ int sip_create(sip_ctx **out, int device, void *stream) {
 }
 
 int sip_destroy(sip_ctx *ctx) {
+  if (!ctx) return SIP_OK;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (void *v : ctx->pinned) cudaFreeHost(v);
+  if (ctx->mempool) cudaMemPoolDestroy(ctx->mempool);
   delete ctx;
   return SIP_OK;
 }
@@ -991,9 +1057,11 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     if (!p->a32in && p->mode == SIP_MODE_F32_REFINED) PA(p->arec64, N * na);
   }
   {
-    cudaError_t e = cudaMallocHost(&p->h_ctl, 3 * sizeof(Ctl));
-    if (e == cudaSuccess) e = cudaMallocHost(&p->h_status, 2 * sizeof(int));
-    if (e != cudaSuccess) return bail(e, "pinned control block");
+    static_assert(3 * sizeof(Ctl) + 2 * sizeof(int) <= kPinnedBlock, "pinned control block");
+    void *blk = pinned_take(ctx);
+    if (!blk) return bail(cudaErrorMemoryAllocation, "pinned control block");
+    p->h_ctl = static_cast<Ctl *>(blk);
+    p->h_status = reinterpret_cast<int *>(static_cast<unsigned char *>(blk) + 3 * sizeof(Ctl));
   }
   cudaStream_t st = ctx->stream;
   std::vector<HaloEntry> hents;
@@ -1266,13 +1334,13 @@ int sip_residual_norm(sip_ctx *ctx, const sip_block_desc *blk, double *rnorm_out
   CU(cudaSetDevice(ctx->device));
   const long long np = resnorm_parts(nb);
   double *scratch = nullptr;
-  CU(cudaMalloc(&scratch, (size_t)(2 * np + 2) * sizeof(double)));
+  CU(ctx_alloc(ctx, (void **)&scratch, (size_t)(2 * np + 2) * sizeof(double)));
   double out[2] = {0.0, 0.0};
   cudaError_t e = launch_resnorm(nb, scratch, scratch + 2 * np, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out, scratch + 2 * np, sizeof(out), cudaMemcpyDeviceToHost, ctx->stream);
+  ctx_free(ctx, scratch);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  cudaFree(scratch);
   if (e != cudaSuccess) return fail(ctx, SIP_ERR_CUDA, std::string("residual norm: ") + cudaGetErrorString(e));
   if (rnorm_out) *rnorm_out = out[0];
   if (bnorm_out) *bnorm_out = out[1];
