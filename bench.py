@@ -252,7 +252,9 @@ def run_reference(args):
         "config": {"workload": f"poisson_{n}cube", "cells": blk.n, "alpha": 0.92,
                    "step": "one FP64 SIP iteration (residual, forward, backward, update, norm)"},
         "cpu_baseline": {"value": value, "unit": "MLUP/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} FP64 SIP iterations of the {n}^3 Poisson block, 1 thread"},
+                         "sample": f"{args.steps} FP64 SIP iterations of the {n}^3 Poisson block, 1 thread",
+                         "host": host_cpu()},
+        "paper_cpu_context": PAPER_CPU,
         "e2e": {"value": value, "unit": "MLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
