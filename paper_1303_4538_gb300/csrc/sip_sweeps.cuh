@@ -606,7 +606,8 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
     const long long kface = (long long)B.nsteps_max * TK * W;  // K faces follow the J faces
     int chunk = 0, cb = -C;  // row-base chunk of issue steps [cb, cb + C)
     const int kchunk = g.k0 + w * Q + lane % Q;
-    // the block's arrays (cell offsets inside a block fit in 32 bits)
+    // the block's arrays (cell offsets inside a block fit in 32 bits; a
+    // record offset, 4 values a cell, is scaled in 64 bits)
     const T *recb = P.rec + B.cell0 * 4;
     const T *rb = P.r + B.cell0;
     T *yb = P.y + B.cell0;
@@ -642,7 +643,7 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
         for (int q = 0; q < Q; ++q) {
           const int o = v[q] ? off[q] : 0;
           unsigned char *d = st + ((size_t)q * NT + tid) * RBY;
-          const unsigned char *src = reinterpret_cast<const unsigned char *>(recb + o * 4);
+          const unsigned char *src = reinterpret_cast<const unsigned char *>(recb + (size_t)o * 4);
 #pragma unroll
           for (int z = 0; z < RBY / 16; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v[q]);
           cp_async_zfill<sizeof(T)>(sr + q * NT, rb + o, v[q]);
@@ -839,7 +840,7 @@ __global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
         for (int q = 0; q < Q; ++q) {
           const int o = v[q] ? off[q] : 0;
           unsigned char *d = st + ((size_t)q * NT + tid) * RBY;
-          const unsigned char *src = reinterpret_cast<const unsigned char *>(recb + o * 4);
+          const unsigned char *src = reinterpret_cast<const unsigned char *>(recb + (size_t)o * 4);
 #pragma unroll
           for (int z = 0; z < RBY / 16; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v[q]);
           cp_async_zfill<sizeof(T)>(sc + (SY + q) * NT, yb + o, v[q]);
