@@ -129,9 +129,13 @@ void sip_default_options(sip_options *opt);
 /* Creates a context on CUDA device `device`, ordering all work on `stream`
  * (a cudaStream_t; NULL = legacy default stream).  *ctx (host) receives the
  * handle.  The context's plans take device memory from its own
- * stream-ordered pool (allocated and freed in `stream` order, up to 1 GiB
- * kept cached between plans), so creating or destroying a plan does not
- * synchronise the device.  Errors: SIP_ERR_NO_DEVICE, SIP_ERR_INVALID_ARG. */
+ * stream-ordered pool (allocated and freed in `stream` order), so creating or
+ * destroying a plan does not synchronise the device.  The pool keeps freed
+ * memory cached for the next plans: at least 1 GiB, and as much as the
+ * largest plan creation on this context used at once (its footprint plus the
+ * factorisation's temporary input), so re-creating a plan of the same size
+ * maps no new memory; sip_destroy returns it all.
+ * Errors: SIP_ERR_NO_DEVICE, SIP_ERR_INVALID_ARG. */
 int sip_create(sip_ctx **ctx, int device, void *stream);
 /* Synchronises the stream and frees the context, its pool and cached pinned
  * blocks.  Destroy the context's plans first. */

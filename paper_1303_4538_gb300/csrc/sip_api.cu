@@ -39,6 +39,11 @@ struct sip_ctx {
   // admit and retire requests while other slots' kernels run.  Null: plain
   // cudaMalloc / cudaFree.
   cudaMemPool_t mempool = nullptr;
+  // bytes the pool keeps cached across synchronisations: at least kPoolKeep,
+  // raised to the largest footprint a plan creation reached unless the
+  // context serves a solve server slot (whose requests are budgeted)
+  unsigned long long pool_keep = 0;
+  bool keep_peak = true;
   // pinned host control blocks of destroyed plans, reused by the next plans
   std::mutex pin_mu;
   std::vector<void *> pinned;
@@ -47,6 +52,12 @@ constexpr size_t kPinnedBlock = 256;  // 3 Ctl + 2 status words, rounded up
 constexpr unsigned long long kPoolKeep = 1ull << 30;  // bytes a context's pool keeps cached
 
 static std::string g_create_error = "no error";
+
+namespace sipk {
+void ctx_keep_peak(sip_ctx *ctx, bool on) {
+  if (ctx) ctx->keep_peak = on;
+}
+}  // namespace sipk
 
 namespace {
 
@@ -165,6 +176,21 @@ cudaError_t ctx_alloc(sip_ctx *ctx, void **v, size_t b) {
 void ctx_free(sip_ctx *ctx, void *v) {
   if (ctx->mempool) cudaFreeAsync(v, ctx->stream);
   else cudaFree(v);
+}
+
+// After a plan's allocations: keep the pool's peak cached, so that creating
+// a plan of the same size again re-maps no memory.
+void pool_keep_peak(sip_ctx *ctx) {
+  if (!ctx->mempool || !ctx->keep_peak) return;
+  unsigned long long hi = 0;
+  if (cudaMemPoolGetAttribute(ctx->mempool, cudaMemPoolAttrUsedMemHigh, &hi) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (hi > ctx->pool_keep && cudaMemPoolSetAttribute(ctx->mempool, cudaMemPoolAttrReleaseThreshold, &hi) ==
+                                 cudaSuccess)
+    ctx->pool_keep = hi;
+  cudaGetLastError();
 }
 
 void *pinned_take(sip_ctx *ctx) {
@@ -745,8 +771,9 @@ int sip_create(sip_ctx **out, int device, void *stream) {
   ctx->smem_optin = prop.sharedMemPerBlockOptin;
   {
     // the context's stream-ordered pool (falls back to cudaMalloc if the
-    // device or driver has none); keeps up to kPoolKeep bytes cached between
-    // plans instead of returning them at every synchronisation
+    // device or driver has none); keeps at least kPoolKeep bytes, and the
+    // largest plan footprint reached, cached between plans instead of
+    // returning them at every synchronisation
     int pools = 0;
     cudaDeviceGetAttribute(&pools, cudaDevAttrMemoryPoolsSupported, device);
     if (pools) {
@@ -758,6 +785,7 @@ int sip_create(sip_ctx **out, int device, void *stream) {
       if (cudaMemPoolCreate(&ctx->mempool, &props) == cudaSuccess) {
         unsigned long long keep = kPoolKeep;
         cudaMemPoolSetAttribute(ctx->mempool, cudaMemPoolAttrReleaseThreshold, &keep);
+        ctx->pool_keep = keep;
       } else {
         ctx->mempool = nullptr;
         cudaGetLastError();
@@ -1056,6 +1084,7 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     PA(p->y32, N);
     if (!p->a32in && p->mode == SIP_MODE_F32_REFINED) PA(p->arec64, N * na);
   }
+  pool_keep_peak(ctx);
   {
     static_assert(3 * sizeof(Ctl) + 2 * sizeof(int) <= kPinnedBlock, "pinned control block");
     void *blk = pinned_take(ctx);
@@ -1135,42 +1164,22 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     const size_t es = f64 ? 8 : 4;
     if (e == cudaSuccess) e = cudaMemsetAsync(p->recF, 0, (size_t)N * 4 * es, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->recB, 0, (size_t)N * 4 * es, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->recA, 0, (size_t)N * na * es, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(a7, 0, (size_t)N * 8 * sizeof(double), st);
-    if (e == cudaSuccess && p->arec64) e = cudaMemsetAsync(p->arec64, 0, (size_t)N * na * 8, st);
     // host vectors must outlive the async copies
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bail(e, "plan upload");
   }
   // A into the plan: the factorisation input (all seven entries, FP64), the
   // A records of the residual in the sweep precision and, in the refined
-  // mode with FP64 coefficients, the FP64 A of the outer residual.
-  // Coefficients that point out of their block are zeroed.
-  {
-    static const int zface[7] = {0, 1, 2, 3, 4, 5, 6};          // ap aw ae as an ab at
-    static const int shift_src[7] = {-1, 2, -1, 4, -1, 6, -1};  // symmetric: aw<-ae, as<-an, ab<-at
-    static const int shift_axis[7] = {0, 1, 0, 2, 0, 3, 0};
-    // slot of entry q in the A records (-1: not stored)
-    const int aslot_s[7] = {0, -1, 1, -1, 2, -1, 3};
-    const int aslot_g[7] = {0, 1, 2, 3, 4, 5, 6};
-    for (auto &bh : p->blocks) {
-      const void *src[7] = {bh.d.ap, bh.d.aw, bh.d.ae, bh.d.as, bh.d.an, bh.d.ab, bh.d.at};
-      const int cd = bh.d.coef_dtype;
-      for (int q = 0; q < 7; ++q) {
-        const void *s = src[q];
-        int sh = 0;
-        if (sym && (q == 1 || q == 3 || q == 5)) {
-          s = src[shift_src[q]];
-          sh = shift_axis[q];
-        }
-        const int zf = sh ? 0 : zface[q];
-        cudaError_t e = launch_to_records(s, cd, a7, 0, 8, q, bh.db, zf, sh, st);
-        const int as = sym ? aslot_s[q] : aslot_g[q];
-        if (e == cudaSuccess && as >= 0) e = launch_to_records(s, cd, p->recA, f64 ? 0 : 1, na, as, bh.db, zf, sh, st);
-        if (e == cudaSuccess && p->arec64 && as >= 0) e = launch_to_records(s, cd, p->arec64, 0, na, as, bh.db, zf, sh, st);
-        if (e != cudaSuccess) return bail(e, "reorder A");
-      }
-    }
+  // mode with FP64 coefficients, the FP64 A of the outer residual (one pass
+  // per block; coefficients that point out of their block are zeroed).
+  for (auto &bh : p->blocks) {
+    PackSrc ps;
+    const void *src[7] = {bh.d.ap, bh.d.aw, bh.d.ae, bh.d.as, bh.d.an, bh.d.ab, bh.d.at};
+    for (int q = 0; q < 7; ++q) ps.a[q] = src[q];
+    ps.f32 = bh.d.coef_dtype;
+    ps.sym = sym ? 1 : 0;
+    cudaError_t e = launch_pack_records(ps, bh.db, a7, p->recA, f64 ? 0 : 1, p->arec64, st);
+    if (e != cudaSuccess) return bail(e, "reorder A");
   }
   // Stone's factorisation (one wavefront sweep)
   {

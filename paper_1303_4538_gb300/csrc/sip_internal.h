@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+struct sip_ctx;  // include/sip.h
+
 namespace sipk {
 
 // device status word values (host maps them to SIP_ERR_*)
@@ -147,9 +149,19 @@ cudaError_t launch_resrow(const RowParams<TA, TX, TR> &prm, bool sym, int grid, 
 template <typename TA, typename TX, typename TR>
 int resrow_max_active(bool sym, bool norm);
 
+// context pool policy (sip_api.cu): whether plan creations raise the
+// pool's cached bytes to their peak footprint (default on)
+void ctx_keep_peak(sip_ctx *ctx, bool on);
+
 // utilities (sip_util.cu)
-cudaError_t launch_to_records(const void *src, int src_is_f32, void *dst, int dst_is_f32, int stride, int slot,
-                              const DevBlock &hb, int zero_face, int shift_axis, cudaStream_t st);
+// the seven coefficient arrays of a block (natural layout, FP32 or FP64;
+// symmetric: aw, as, ab are taken from the neighbours' ae, an, at)
+struct PackSrc {
+  const void *a[7];  // ap aw ae as an ab at
+  int f32, sym;
+};
+cudaError_t launch_pack_records(const PackSrc &S, const DevBlock &hb, double *a7, void *recA, int recA_f32,
+                                double *arec64, cudaStream_t st);
 cudaError_t launch_to_plan_f64(const double *src, double *dst, const DevBlock &hb, cudaStream_t st);
 cudaError_t launch_from_plan_f64(const double *src, double *dst, const DevBlock &hb, cudaStream_t st);
 cudaError_t launch_sumsq_partials(const double *v, long long n, double *partials, int nparts,

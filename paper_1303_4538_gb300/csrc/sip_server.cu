@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "../../include/sip.h"
+#include "sip_internal.h"
 
 namespace {
 
@@ -86,6 +87,8 @@ void slot_loop(sip_server *s, int slot) {
   sip_ctx *ctx = nullptr;
   const bool ok = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess &&
                   sip_create(&ctx, s->device, stream) == SIP_OK;
+  // the slot's pool keeps its fixed cache only: requests are budgeted
+  if (ok) sipk::ctx_keep_peak(ctx, false);
   for (;;) {
     Request r{};
     r.ticket = 0;

@@ -41,71 +41,132 @@ __device__ __forceinline__ long long plan_cell(const DevBlock &hb, int i, int j,
   return hb.cell0 + plane_row_base(hb.PO, hb.F, hb.mmax, hb.nx, i + j + k, k) + j;
 }
 
-// natural index p = i + nx*(j + ny*k)  ->  record slot `slot` of plan cell
-// (records of `stride` values, FP32 or FP64).
-// zero_face: 0 keep; 1..6 zero the coefficient on the face i=0, i=nx-1,
-// j=0, j=ny-1, k=0, k=nz-1 (an entry that points out of the block).
-// shift_axis: 0 read src[p]; 1/2/3 read src at the lower neighbour along
-// i/j/k (0 on the lower face): builds AW/AS/AB of a symmetric matrix from AE/AN/AT.
-__global__ void k_to_records(const void *src, int src_is_f32, void *dst, int dst_is_f32, int stride, int slot,
-                             DevBlock hb, int zero_face, int shift_axis) {
-  const long long n = (long long)hb.nx * hb.ny * hb.nz;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-       p += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(p % hb.nx);
-    const int j = (int)((p / hb.nx) % hb.ny);
-    const int k = (int)(p / ((long long)hb.nx * hb.ny));
-    bool zero = (zero_face == 1 && i == 0) || (zero_face == 2 && i == hb.nx - 1) ||
-                (zero_face == 3 && j == 0) || (zero_face == 4 && j == hb.ny - 1) ||
-                (zero_face == 5 && k == 0) || (zero_face == 6 && k == hb.nz - 1);
-    long long q = p;
-    if (shift_axis == 1) { if (i == 0) zero = true; else q = p - 1; }
-    if (shift_axis == 2) { if (j == 0) zero = true; else q = p - hb.nx; }
-    if (shift_axis == 3) { if (k == 0) zero = true; else q = p - (long long)hb.nx * hb.ny; }
-    double v = 0.0;
-    if (!zero && src) v = src_is_f32 ? (double)((const float *)src)[q] : ((const double *)src)[q];
-    const long long a = plan_cell(hb, i, j, k) * stride + slot;
-    if (dst_is_f32) ((float *)dst)[a] = (float)v;
-    else ((double *)dst)[a] = v;
+// Walk over a block's natural rows (j, k): one warp per row, lanes stepping
+// along i, so the natural-layout side of every copy is coalesced and the index
+// arithmetic stays in 32 bits (a block has fewer than 2^31 cells).  f(i, j, k,
+// p, c) gets the natural index p = i + nx (j + ny k) and the plan cell c.
+constexpr int kWalkThreads = 256;
+
+static int walk_grid(const DevBlock &hb) {
+  const long long rows = (long long)hb.ny * hb.nz;
+  long long g = (rows + kWalkThreads / 32 - 1) / (kWalkThreads / 32);
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <typename Fn>
+__device__ __forceinline__ void walk_rows(const DevBlock &hb, Fn &&f) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int nrows = hb.ny * hb.nz;
+  for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < nrows; r += gridDim.x * wpb) {
+    const int k = r / hb.ny, j = r - k * hb.ny;
+    const int p0 = r * hb.nx;
+    for (int i = lane; i < hb.nx; i += 32) {
+      const long long c = hb.cell0 + plane_row_base(hb.PO, hb.F, hb.mmax, hb.nx, i + j + k, k) + j;
+      f(i, j, k, p0 + i, c);
+    }
   }
 }
 
-cudaError_t launch_to_records(const void *src, int src_is_f32, void *dst, int dst_is_f32, int stride, int slot,
-                              const DevBlock &hb, int zf, int sh, cudaStream_t st) {
-  k_to_records<<<util_grid((long long)hb.nx * hb.ny * hb.nz), 256, 0, st>>>(src, src_is_f32, dst, dst_is_f32,
-                                                                            stride, slot, hb, zf, sh);
+// The seven matrix entries of every cell into the plan's records, one pass:
+// the factorisation input a7 [AP AW AE AS AN AB AT 0] (FP64), the residual's
+// A record in the sweep precision (symmetric [AP AE AN AT], general the a7
+// order) and, where given, its FP64 copy.  Entries that point out of the
+// block are zeroed; a symmetric matrix takes AW, AS, AB from the lower
+// neighbour's AE, AN, AT (0 on the lower faces).  Whole records are written,
+// so the destinations need no clearing.
+template <typename TR>
+__global__ void __launch_bounds__(kWalkThreads) k_pack_records(PackSrc S, DevBlock hb, double *a7, TR *recA,
+                                                                double *arec64) {
+  const int nxy = hb.nx * hb.ny;
+  auto ld = [&](int q, int p) -> double {
+    const void *a = S.a[q];
+    if (!a) return 0.0;
+    return S.f32 ? (double)static_cast<const float *>(a)[p] : static_cast<const double *>(a)[p];
+  };
+  walk_rows(hb, [&](int i, int j, int k, int p, long long c) {
+    double v[7];
+    v[0] = ld(0, p);
+    v[2] = i < hb.nx - 1 ? ld(2, p) : 0.0;
+    v[4] = j < hb.ny - 1 ? ld(4, p) : 0.0;
+    v[6] = k < hb.nz - 1 ? ld(6, p) : 0.0;
+    if (S.sym) {
+      v[1] = i > 0 ? ld(2, p - 1) : 0.0;
+      v[3] = j > 0 ? ld(4, p - hb.nx) : 0.0;
+      v[5] = k > 0 ? ld(6, p - nxy) : 0.0;
+    } else {
+      v[1] = i > 0 ? ld(1, p) : 0.0;
+      v[3] = j > 0 ? ld(3, p) : 0.0;
+      v[5] = k > 0 ? ld(5, p) : 0.0;
+    }
+    double2 *d7 = reinterpret_cast<double2 *>(a7 + c * 8);
+    d7[0] = make_double2(v[0], v[1]);
+    d7[1] = make_double2(v[2], v[3]);
+    d7[2] = make_double2(v[4], v[5]);
+    d7[3] = make_double2(v[6], 0.0);
+    if (S.sym) {
+      const double r4[4] = {v[0], v[2], v[4], v[6]};
+      if constexpr (sizeof(TR) == 4) {
+        reinterpret_cast<float4 *>(recA)[c] = make_float4((float)r4[0], (float)r4[1], (float)r4[2], (float)r4[3]);
+      } else {
+        double2 *d = reinterpret_cast<double2 *>(recA + c * 4);
+        d[0] = make_double2(r4[0], r4[1]);
+        d[1] = make_double2(r4[2], r4[3]);
+      }
+      if (arec64) {
+        double2 *d = reinterpret_cast<double2 *>(arec64 + c * 4);
+        d[0] = make_double2(r4[0], r4[1]);
+        d[1] = make_double2(r4[2], r4[3]);
+      }
+    } else {
+      if constexpr (sizeof(TR) == 4) {
+        float4 *d = reinterpret_cast<float4 *>(recA + c * 8);
+        d[0] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+        d[1] = make_float4((float)v[4], (float)v[5], (float)v[6], 0.0f);
+      } else {
+        double2 *d = reinterpret_cast<double2 *>(recA + c * 8);
+        d[0] = make_double2(v[0], v[1]);
+        d[1] = make_double2(v[2], v[3]);
+        d[2] = make_double2(v[4], v[5]);
+        d[3] = make_double2(v[6], 0.0);
+      }
+      if (arec64) {
+        double2 *d = reinterpret_cast<double2 *>(arec64 + c * 8);
+        d[0] = make_double2(v[0], v[1]);
+        d[1] = make_double2(v[2], v[3]);
+        d[2] = make_double2(v[4], v[5]);
+        d[3] = make_double2(v[6], 0.0);
+      }
+    }
+  });
+}
+
+cudaError_t launch_pack_records(const PackSrc &S, const DevBlock &hb, double *a7, void *recA, int recA_f32,
+                                double *arec64, cudaStream_t st) {
+  if (recA_f32)
+    k_pack_records<float><<<walk_grid(hb), kWalkThreads, 0, st>>>(S, hb, a7, static_cast<float *>(recA), arec64);
+  else
+    k_pack_records<double><<<walk_grid(hb), kWalkThreads, 0, st>>>(S, hb, a7, static_cast<double *>(recA), arec64);
   return cudaGetLastError();
 }
 
-__global__ void k_to_plan(const double *src, double *dst, DevBlock hb) {
-  const long long n = (long long)hb.nx * hb.ny * hb.nz;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-       p += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(p % hb.nx);
-    const int j = (int)((p / hb.nx) % hb.ny);
-    const int k = (int)(p / ((long long)hb.nx * hb.ny));
-    dst[plan_cell(hb, i, j, k)] = src[p];
-  }
+__global__ void __launch_bounds__(kWalkThreads) k_to_plan(const double *src, double *dst, DevBlock hb) {
+  walk_rows(hb, [&](int, int, int, int p, long long c) { dst[c] = src[p]; });
 }
 
 cudaError_t launch_to_plan_f64(const double *src, double *dst, const DevBlock &hb, cudaStream_t st) {
-  k_to_plan<<<util_grid((long long)hb.nx * hb.ny * hb.nz), 256, 0, st>>>(src, dst, hb);
+  k_to_plan<<<walk_grid(hb), kWalkThreads, 0, st>>>(src, dst, hb);
   return cudaGetLastError();
 }
 
-__global__ void k_from_plan(const double *src, double *dst, DevBlock hb) {
-  const long long n = (long long)hb.nx * hb.ny * hb.nz;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-       p += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(p % hb.nx);
-    const int j = (int)((p / hb.nx) % hb.ny);
-    const int k = (int)(p / ((long long)hb.nx * hb.ny));
-    dst[p] = src[plan_cell(hb, i, j, k)];
-  }
+__global__ void __launch_bounds__(kWalkThreads) k_from_plan(const double *src, double *dst, DevBlock hb) {
+  walk_rows(hb, [&](int, int, int, int p, long long c) { dst[p] = src[c]; });
 }
 
 cudaError_t launch_from_plan_f64(const double *src, double *dst, const DevBlock &hb, cudaStream_t st) {
-  k_from_plan<<<util_grid((long long)hb.nx * hb.ny * hb.nz), 256, 0, st>>>(src, dst, hb);
+  k_from_plan<<<walk_grid(hb), kWalkThreads, 0, st>>>(src, dst, hb);
   return cudaGetLastError();
 }
 

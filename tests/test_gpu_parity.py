@@ -2,8 +2,9 @@
 
 Bars (FP64): factors within 1e-13 relative to each array's magnitude; per
 iteration, x within 1e-12 relative (inf-norm) and relres within 1e-12
-absolute.  The differences come only from FMA contraction and the stored
-reciprocal 1/LP on the GPU (the oracle divides, without contraction).
+absolute.  The differences come only from FMA contraction and the
+reciprocal 1/LP on the GPU, stored and multiplied into UN, UE, UT (the
+oracle divides, without contraction).
 """
 import numpy as np
 import pytest
