@@ -2,6 +2,7 @@
 // FP32 factors, inner iterations of the mixed-precision refinement and the
 // pure single-precision relaxation).
 #include "sip_kernels.h"
+#include "sip_factor.cuh"
 #include "sip_sweeps.cuh"
 
 namespace sipk {

@@ -1,6 +1,7 @@
 // sip_k64.cu -- instantiations of the FP64 sweep kernels (factorisation with
 // FP64 factors, FP64 forward / backward substitution).
 #include "sip_kernels.h"
+#include "sip_factor.cuh"
 #include "sip_sweeps.cuh"
 
 namespace sipk {

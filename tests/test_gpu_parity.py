@@ -3,8 +3,8 @@
 Bars (FP64): factors within 1e-13 relative to each array's magnitude; per
 iteration, x within 1e-12 relative (inf-norm) and relres within 1e-12
 absolute.  The differences come only from FMA contraction and the
-reciprocal 1/LP on the GPU, stored and multiplied into UN, UE, UT (the
-oracle divides, without contraction).
+reciprocals on the GPU: 1/LP, stored and multiplied into UN, UE, UT, and
+1/(dB dW dS) for LB, LW, LS (the oracle divides, without contraction).
 """
 import numpy as np
 import pytest
