@@ -210,14 +210,16 @@ def cpu_baseline(blk, iters: int):
     import numpy as np
     import oracle
     n = blk.nx
+    t0 = time.perf_counter()
     F = oracle.factor(n, n, n, blk.coefs, 0.92)
+    tf = time.perf_counter() - t0
     x = np.zeros(blk.n)
     oracle.iterate(n, n, n, blk.coefs, F, blk.b, x)  # warm
     t0 = time.perf_counter()
     for _ in range(iters):
         oracle.iterate(n, n, n, blk.coefs, F, blk.b, x)
     dt = time.perf_counter() - t0
-    return blk.n * iters / dt / 1e6, dt
+    return blk.n * iters / dt / 1e6, dt, tf
 
 
 def run_reference(args):
@@ -431,10 +433,17 @@ def run_gb300(args):
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        v, dt = cpu_baseline(blk, args.cpu_iters)
+        v, dt, tf = cpu_baseline(blk, args.cpu_iters)
         cpu = {"value": v, "unit": "MLUP/s", "cores": 1, "kind": "oracle",
                "sample": f"{args.cpu_iters} FP64 SIP iterations of the {args.n}^3 Poisson block "
-                         f"({dt:.1f} s, plain C, 1 thread)", "host": host_cpu()}
+                         f"({dt:.1f} s, plain C, 1 thread)", "host": host_cpu(),
+               "factor_s": round(tf, 3)}
+        if ttol and "f64" in ttol:
+            # the oracle's seconds per iteration times the iterations the
+            # device's FP64 solve needed to reach 1e-8 (not run: extrapolated)
+            its = ttol["f64"]["iterations"]
+            cpu["time_to_1e-8_s"] = {"value": round(dt / args.cpu_iters * its, 1), "extrapolated": True,
+                                     "iterations": its}
     line = {
         "metric": METRIC, "value": round(val_r, 1), "unit": "MLUP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_r / args.steps, 3), "higher_is_better": True,
@@ -578,6 +587,24 @@ def large(args, local):
     out["f64_alpha092_relres"] = {"min": min(h), "at_40": h[-1], "diverges": bool(h[-1] > 4 * min(h))}
     plan.close()
     ctx.close()
+    if not args.no_cpu_baseline:
+        # the oracle (plain C, one thread) on the same block: its factorisation
+        # and one FP64 SIP iteration at alpha 0.5, and its time to 1e-8
+        # extrapolated with the device's FP64 iteration count
+        import oracle
+        n = blk.nx
+        t0 = time.perf_counter()
+        F = oracle.factor(n, n, n, blk.coefs, 0.5)
+        tf = time.perf_counter() - t0
+        xo = np.zeros(blk.n)
+        t0 = time.perf_counter()
+        oracle.iterate(n, n, n, blk.coefs, F, blk.b, xo)
+        ti = time.perf_counter() - t0
+        its = out["f64_alpha05"]["iterations"]
+        out["cpu_oracle"] = {"kind": "oracle", "cores": 1, "host": host_cpu(), "factor_s": round(tf, 2),
+                             "s_per_iteration": round(ti, 3), "MLUP_per_s": round(blk.n / ti / 1e6, 1),
+                             "time_to_1e-8_s": {"value": round(ti * its, 1), "extrapolated": True,
+                                                "iterations": its}}
     return out
 
 
