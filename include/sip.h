@@ -140,6 +140,11 @@ int sip_create(sip_ctx **ctx, int device, void *stream);
 /* Synchronises the stream and frees the context, its pool and cached pinned
  * blocks.  Destroy the context's plans first. */
 int sip_destroy(sip_ctx *ctx);
+/* Synchronises the stream and returns the pool's cached memory (everything
+ * not held by a live plan) to the device; the cache limit drops back to
+ * 1 GiB until the next plan creation raises it.  Live plans are unaffected.
+ * Errors: SIP_ERR_INVALID_ARG (ctx NULL), SIP_ERR_CUDA. */
+int sip_trim(sip_ctx *ctx);
 /* Description of the last error on ctx (never NULL; valid until the next
  * call on this thread).  ctx == NULL: the last sip_create failure. */
 const char *sip_last_error(sip_ctx *ctx);

@@ -824,6 +824,20 @@ int sip_destroy(sip_ctx *ctx) {
   return SIP_OK;
 }
 
+int sip_trim(sip_ctx *ctx) {
+  if (!ctx) return SIP_ERR_INVALID_ARG;
+  cudaSetDevice(ctx->device);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess && ctx->mempool) {
+    unsigned long long keep = kPoolKeep;
+    e = cudaMemPoolTrimTo(ctx->mempool, 0);
+    if (e == cudaSuccess) e = cudaMemPoolSetAttribute(ctx->mempool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e == cudaSuccess) ctx->pool_keep = keep;
+  }
+  if (e != cudaSuccess) return fail(ctx, SIP_ERR_CUDA, std::string("trim: ") + cudaGetErrorString(e));
+  return SIP_OK;
+}
+
 const char *sip_last_error(sip_ctx *ctx) {
   static thread_local std::string copy;
   copy = ctx ? ctx->err : g_create_error;

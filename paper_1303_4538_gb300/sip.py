@@ -39,7 +39,7 @@ ERROR_NAMES = {
 
 # every symbol include/sip.h declares
 EXPORTED = (
-    "sip_default_options", "sip_create", "sip_destroy", "sip_last_error", "sip_factor",
+    "sip_default_options", "sip_create", "sip_destroy", "sip_trim", "sip_last_error", "sip_factor",
     "sip_iterate", "sip_solve", "sip_get_history", "sip_export_factors", "sip_plan_bytes", "sip_plan_shape",
     "sip_plan_destroy", "sip_plane_layout", "sip_profile_enable", "sip_profile_read",
     "sip_launch_count", "sip_kernel_name", "sip_residual_norm",
@@ -106,6 +106,7 @@ def lib():
         L.sip_default_options.restype = None
         L.sip_create.argtypes = [ctypes.POINTER(P), I, P]
         L.sip_destroy.argtypes = [P]
+        L.sip_trim.argtypes = [P]
         L.sip_last_error.argtypes = [P]
         L.sip_last_error.restype = ctypes.c_char_p
         L.sip_factor.argtypes = [P, ctypes.POINTER(sip_block_desc), I, ctypes.POINTER(sip_interface), I,
@@ -180,6 +181,11 @@ class Context:
         """sip_residual_norm_noalloc: writes (||b - A x||_2, ||b||_2) into the
         device array `out` (2 doubles) in stream order; no allocation, no sync."""
         self.check(lib().sip_residual_norm_noalloc(self.h, ctypes.byref(desc), ctypes.c_void_p(_ptr(out))))
+
+    def trim(self) -> None:
+        """sip_trim: return the pool's cached device memory (not held by a
+        live plan) to the device."""
+        self.check(lib().sip_trim(self.h))
 
     def close(self):
         if self.h:

@@ -92,3 +92,9 @@ def test_no_cpu_fallback_without_gpu():
 def test_default_options():
     o = sip.default_options()
     assert o.alpha == pytest.approx(0.92) and o.mode == sip.SIP_MODE_F64 and o.inner_iters == 4
+
+
+def test_null_handles_are_invalid_arguments():
+    L = sip.lib()
+    assert L.sip_trim(None) == sip.SIP_ERR_INVALID_ARG
+    assert L.sip_destroy(None) == sip.SIP_OK
