@@ -56,7 +56,7 @@ ALGO_BYTES = {
 }
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -81,7 +81,7 @@ def parse():
                     help="also solve the 384^3 Peclet-10 block with FP32 coefficients (alpha 0.5 and 0.92)")
     ap.add_argument("--batched-iters", type=int, default=12,
                     help="corrections (refined) / iterations (fp64) timed on the batched mesh")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():

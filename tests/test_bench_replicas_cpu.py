@@ -48,3 +48,34 @@ def test_dist_env_defaults_to_one_rank(monkeypatch):
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
         monkeypatch.delenv(k, raising=False)
     assert bench.dist_env() == (0, 1, 0)
+
+
+def _ref_worker(rank, world, port, outdir):
+    import contextlib
+    import json as _json
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    args = bench.parse(["--impl", "reference", "--gpus", str(world), "--steps", "2", "--warmup", "1",
+                             "--n", "12"])
+    path = os.path.join(outdir, f"rank{rank}.out")
+    with open(path, "w") as f, contextlib.redirect_stdout(f):
+        bench.run_reference(args)
+    lines = [l for l in open(path) if l.strip()]
+    if lines:
+        _json.loads(lines[0])
+
+
+def test_reference_arm_two_ranks_rank0_prints_one_line(tmp_path):
+    """Under two ranks the reference arm (the oracle on the host) runs and
+    prints on rank 0 only; rank 1 exits without work."""
+    import json
+    world = 2
+    mp.spawn(_ref_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    out0 = [l for l in open(tmp_path / "rank0.out") if l.strip()]
+    out1 = [l for l in open(tmp_path / "rank1.out") if l.strip()]
+    assert len(out0) == 1 and out1 == []
+    line = json.loads(out0[0])
+    assert line["impl"] == "reference" and line["unit"] == "MLUP/s" and line["value"] > 0
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["n_gpus"] == 2
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
