@@ -829,10 +829,15 @@ int sip_trim(sip_ctx *ctx) {
   cudaSetDevice(ctx->device);
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e == cudaSuccess && ctx->mempool) {
-    unsigned long long keep = kPoolKeep;
+    unsigned long long keep = kPoolKeep, zero = 0;
     e = cudaMemPoolTrimTo(ctx->mempool, 0);
     if (e == cudaSuccess) e = cudaMemPoolSetAttribute(ctx->mempool, cudaMemPoolAttrReleaseThreshold, &keep);
     if (e == cudaSuccess) ctx->pool_keep = keep;
+    // restart the peak from what live plans hold, so the next plan creation
+    // raises the cache limit to its own peak only (best effort: without the
+    // reset the limit returns to the earlier peak)
+    if (e == cudaSuccess && cudaMemPoolSetAttribute(ctx->mempool, cudaMemPoolAttrUsedMemHigh, &zero) != cudaSuccess)
+      cudaGetLastError();
   }
   if (e != cudaSuccess) return fail(ctx, SIP_ERR_CUDA, std::string("trim: ") + cudaGetErrorString(e));
   return SIP_OK;
