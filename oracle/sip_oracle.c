@@ -50,7 +50,7 @@
  * Parity status: the factorisation is pinned by the defining identity
  * L U = A + N, by alpha = 0 (ILU(0)) and by the 1-D case (exact LU); the
  * iteration by the dense preconditioned-Richardson step and by convergence to
- * the dense solution; the single-precision and refinement drivers by
+ * the dense solution; the single-precision and refinement solve loops by
  * convergence to the FP64 solution; the single-precision solve by tracking the
  * FP64 history until it stagnates at the float level; the multi-block solve by the dense
  * global residual, the dense block-Jacobi Richardson step and convergence to

@@ -771,7 +771,7 @@ int sip_create(sip_ctx **out, int device, void *stream) {
   ctx->smem_optin = prop.sharedMemPerBlockOptin;
   {
     // the context's stream-ordered pool (falls back to cudaMalloc if the
-    // device or driver has none); keeps at least kPoolKeep bytes, and the
+    // device or the CUDA driver has none); keeps at least kPoolKeep bytes, and the
     // largest plan footprint reached, cached between plans instead of
     // returning them at every synchronisation
     int pools = 0;

@@ -1,6 +1,6 @@
 """The context's memory pool: a destroyed plan's memory stays cached for the
 next plan of the same size (no new device memory is mapped), and sip_trim
-returns it to the device.  Free memory is read from the driver
+returns it to the device.  Free memory is read from the CUDA driver
 (cudaMemGetInfo through torch), outside the library."""
 import pytest
 import torch
