@@ -156,9 +156,11 @@ def src_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def load_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+def load_traffic(kernel: str, cells: int):
+    """DRAM bytes of one launch over `cells` cells from the committed ncu
+    summary (its bytes per captured cell: every array is touched once per
+    launch, so the traffic grows in proportion to the cells), if the capture
+    was taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))
@@ -167,7 +169,9 @@ def load_traffic(kernel: str):
     if d.get("src_hash") != src_hash():
         return None
     v = d.get("kernels", {}).get(kernel)
-    return v.get("bytes_per_launch_full") if isinstance(v, dict) else None
+    if not isinstance(v, dict) or not v.get("captured_cells"):
+        return None
+    return int(round(v["captured_bytes"] / v["captured_cells"] * cells))
 
 
 def peaks():
@@ -422,7 +426,7 @@ def run_gb300(args):
         per_launch_s = tot_ms / n / 1e3
         ach = ALGO_BYTES[k] * N / per_launch_s / 1e9
         return {"bound": "hbm", "kernel": k, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(ach / hbm, 4), "traffic": load_traffic(k), "peak_source": src,
+                "frac": round(ach / hbm, 4), "traffic": load_traffic(k, N), "peak_source": src,
                 "algo_bytes_per_cell": ALGO_BYTES[k], "cells_per_launch": N,
                 "avg_launch_us": round(per_launch_s * 1e6, 2),
                 "share": round(tot_ms / sum(v[0] for v in prof.values()), 4)}

@@ -79,3 +79,23 @@ def test_reference_arm_two_ranks_rank0_prints_one_line(tmp_path):
     assert line["steps"] == 2 and line["warmup"] == 1 and line["n_gpus"] == 2
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_traffic_counters_scale_with_cells_and_expire_with_the_sources(monkeypatch):
+    """The committed DRAM counters are per captured cell, taken on the current
+    sweep sources; a changed source hash makes them unavailable (null)."""
+    import json
+    d = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
+    current = d["src_hash"] == bench.src_hash()
+    for kernel, v in d["kernels"].items():
+        assert kernel in bench.ALGO_BYTES
+        per_cell = v["captured_bytes"] / v["captured_cells"]
+        # DRAM traffic within the algorithmic bytes plus the records' pad words
+        assert 0.5 * bench.ALGO_BYTES[kernel] <= per_cell <= 1.25 * bench.ALGO_BYTES[kernel], kernel
+        if current:
+            assert bench.load_traffic(kernel, 1000) == round(per_cell * 1000)
+            assert bench.load_traffic(kernel, 2000) == round(per_cell * 2000)
+        else:  # counters of other sources are never reported
+            assert bench.load_traffic(kernel, 1000) is None
+    monkeypatch.setattr(bench, "src_hash", lambda: "0" * 16)
+    assert bench.load_traffic("fwd32", 1000) is None
