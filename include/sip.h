@@ -216,7 +216,12 @@ int sip_residual_norm(sip_ctx *ctx, const sip_block_desc *blk, double *rnorm_out
  *     threads) race on that array: the caller must order them;
  *   - the first call on each device looks the array's address up (and may
  *     load the library's device code); make it before any stream capture
- *     begins and outside time-critical code.
+ *     begins and outside time-critical code.  The address is cached for the
+ *     life of the device's primary context: after cudaDeviceReset, calls on
+ *     that device are unsafe until the process restarts;
+ *   - norms_dev must be device (or managed) memory of the context's device;
+ *     host pointers, other devices' memory and unaligned pointers are
+ *     rejected (SIP_ERR_INVALID_ARG).
  * Errors: SIP_ERR_INVALID_ARG, SIP_ERR_CUDA. */
 #define SIP_NOALLOC_MAX_CELLS 67108864LL
 int sip_residual_norm_noalloc(sip_ctx *ctx, const sip_block_desc *blk, double *norms_dev);

@@ -24,7 +24,9 @@
 //   * the device address of the array is looked up once per device (with
 //     that device current) and cached; that first call may also load this
 //     library's device code, so it belongs before any stream capture and
-//     outside time-critical regions.
+//     outside time-critical regions.  A cudaDeviceReset (or anything else
+//     that destroys the device's primary context) unloads the array, so the
+//     cached address is only valid until then; a failed launch drops it.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -35,9 +37,12 @@ namespace sipk {
 
 static __device__ __align__(256) double g_noalloc_scratch[2 * kNoallocParts];
 
+static std::mutex g_mu;
+static void *g_addr[kNoallocMaxDevices] = {};
+
 cudaError_t noalloc_scratch(int device, double **out) {
-  static std::mutex mu;
-  static void *addr[kNoallocMaxDevices] = {};
+  std::mutex &mu = g_mu;
+  void **addr = g_addr;
   *out = nullptr;
   if (device < 0 || device >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(mu);
@@ -49,6 +54,12 @@ cudaError_t noalloc_scratch(int device, double **out) {
   }
   *out = static_cast<double *>(addr[device]);
   return cudaSuccess;
+}
+
+void noalloc_forget(int device) {
+  if (device < 0 || device >= kNoallocMaxDevices) return;
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_addr[device] = nullptr;
 }
 
 }  // namespace sipk

@@ -161,6 +161,7 @@ class Context:
 
     def __init__(self, device: int = 0, stream: Optional[int] = None):
         self.h = ctypes.c_void_p()
+        self.device = int(device)
         rc = lib().sip_create(ctypes.byref(self.h), int(device), ctypes.c_void_p(stream or 0))
         if rc != SIP_OK:
             raise SipError(rc, "sip_create failed: " + lib().sip_last_error(None).decode())
@@ -180,6 +181,11 @@ class Context:
     def residual_norm_noalloc(self, desc: "sip_block_desc", out) -> None:
         """sip_residual_norm_noalloc: writes (||b - A x||_2, ||b||_2) into the
         device array `out` (2 doubles) in stream order; no allocation, no sync."""
+        if not isinstance(out, int):
+            import torch
+            if not (out.is_cuda and out.dtype == torch.float64 and out.numel() >= 2
+                    and out.device.index == self.device):
+                raise ValueError("out must be a float64 tensor of >= 2 elements on the context's device")
         self.check(lib().sip_residual_norm_noalloc(self.h, ctypes.byref(desc), ctypes.c_void_p(_ptr(out))))
 
     def trim(self) -> None:
