@@ -23,7 +23,6 @@
 #include "../../include/sip.h"
 #include "sip_internal.h"
 #include "sip_kernels.h"
-#include "sip_layout.h"
 
 using namespace sipk;
 
@@ -114,10 +113,7 @@ struct sip_plan {
   std::vector<BlockHost> blocks;
   long long ncells = 0;
   int ntiles = 0;
-  int Q = 2, NW = 8, NT = 256, TK = 16, tab_ints = 0;  // tile rows TK; factorisation CTA (Q rows x NW warps)
-  int sQ = 2, sNWT = 8, sD = 8;  // substitution sweeps: rows per warp, warps per tile, stage depth
-  long long nl = 0;              // elements of the tile layout (cells plus padding)
-  int lead = 4;                  // start slack of the substitution sweeps, in steps
+  int Q = 2, NW = 8, NT = 256, TK = 16, tab_ints = 0;
   int Rk[K_NKINDS] = {};     // stage depth chosen per kernel kind
   int gridk[K_NKINDS] = {};  // resident CTAs per kernel kind (grid of the ticketed sweeps)
   std::vector<void *> allocs;
@@ -276,7 +272,6 @@ SweepCommon common(sip_plan *p, bool backward, int ticket, int reset, int slot, 
   c.faces = p->faces;
   c.status = p->status;
   c.max_spin = p->opt.max_spin > 0 ? p->opt.max_spin : (1ll << 22);
-  c.lead = p->lead;
   return c;
 }
 
@@ -322,17 +317,6 @@ cudaError_t launch(sip_plan *p, int kind, const Params &prm) {
   return cudaLaunchKernel(kernel_ptr(kind, p->Q, R), dim3(grid), dim3(p->NT), args, smem, p->ctx->stream);
 }
 
-// warp-decoupled substitution sweeps (sip_wsweeps.cuh)
-template <typename T>
-cudaError_t launch_w(sip_plan *p, int kind, const WParams<T> &prm) {
-  const size_t smem = wkernel_smem(kind, p->sQ, p->sD, p->sNWT);
-  const int grid = std::max(1, std::min(p->ntiles, p->gridk[kind]));
-  void *args[] = {(void *)&prm};
-  ProfScope ps(p, kind);
-  return cudaLaunchKernel(wkernel_ptr(kind, p->sQ, p->sD), dim3(grid), dim3(32 * p->sNWT), args, smem,
-                          p->ctx->stream);
-}
-
 // utility launches (layout, reductions, control) are counted as kind K_NKINDS
 #define UTIL(call)              \
   do {                          \
@@ -358,7 +342,7 @@ int check_status(sip_plan *p) {
 int enqueue_halo(sip_plan *p) {
   sip_ctx *ctx = p->ctx;
   if (p->nhalo > 0 && p->mode == SIP_MODE_F32)
-    UTIL(launch_cast_f32_f64(p->d32, p->x64, p->nl, ctx->stream));  // the FP32 iterate is the current x
+    UTIL(launch_cast_f32_f64(p->d32, p->x64, p->ncells, ctx->stream));  // the FP32 iterate is the current x
   if (p->nhalo > 0) UTIL(launch_halo(p->halo, p->nhalo, p->b64, p->x64, p->beff64, p->ctl, ctx->stream));
   return SIP_OK;
 }
@@ -388,13 +372,12 @@ int enqueue_resid(sip_plan *p, int kind, const TA *arec, const TX *b, const TX *
 template <typename T>
 int enqueue_forward(sip_plan *p, int kind, const T *r, T *y) {
   sip_ctx *ctx = p->ctx;
-  WParams<T> f;
+  FwdParams<T> f;
   f.c = common(p, false, 0, 1, 0, kind);
   f.rec = (const T *)p->recF;
-  f.sa = r;
-  f.sb = nullptr;
-  f.out = y;
-  CU(launch_w(p, kind, f));
+  f.r = r;
+  f.y = y;
+  CU(launch(p, kind, f));
   return SIP_OK;
 }
 
@@ -402,13 +385,12 @@ int enqueue_forward(sip_plan *p, int kind, const T *r, T *y) {
 template <typename T>
 int enqueue_backward(sip_plan *p, int kind, const T *y, T *x) {
   sip_ctx *ctx = p->ctx;
-  WParams<T> b;
+  BwdParams<T> b;
   b.c = common(p, true, 1, 0, 1, kind);
   b.rec = (const T *)p->recB;
-  b.sa = y;
-  b.sb = kind == K_BWD32Z ? nullptr : x;
-  b.out = x;
-  CU(launch_w(p, kind, b));
+  b.y = y;
+  b.x = x;
+  CU(launch(p, kind, b));
   return SIP_OK;
 }
 
@@ -454,7 +436,7 @@ int enqueue_iter_refined(sip_plan *p) {
   }
   {
     ProfScope ps(p, K_UPD64);
-    CU(launch_update64(p->d32, p->x64, p->nl, p->ctl, ctx->stream));
+    CU(launch_update64(p->d32, p->x64, p->ncells, p->ctl, ctx->stream));
   }
   return SIP_OK;
 }
@@ -465,7 +447,7 @@ int enqueue_iter_refined(sip_plan *p) {
 int enqueue_iter_f32(sip_plan *p) {
   sip_ctx *ctx = p->ctx;
   if (int rc = enqueue_halo(p)) return rc;
-  if (p->nhalo > 0) UTIL(launch_cast_f64_f32(p->beff64, p->r32, p->nl, ctx->stream));
+  if (p->nhalo > 0) UTIL(launch_cast_f64_f32(p->beff64, p->r32, p->ncells, ctx->stream));
   if (int rc = enqueue_resid(p, K_RES32N, (const float *)p->recA, (const float *)p->r32, (const float *)p->d32,
                              p->y32, true))
     return rc;
@@ -539,12 +521,12 @@ int begin_sequence(sip_plan *p, double rtol, int max_iters) {
     UTIL(launch_to_plan_f64(bh.d.x, p->x64, bh.db, ctx->stream));
   }
   if (p->beff64)
-    CU(cudaMemcpyAsync(p->beff64, p->b64, (size_t)p->nl * sizeof(double), cudaMemcpyDeviceToDevice,
+    CU(cudaMemcpyAsync(p->beff64, p->b64, (size_t)p->ncells * sizeof(double), cudaMemcpyDeviceToDevice,
                        ctx->stream));
-  UTIL(launch_sumsq_partials(p->b64, p->nl, p->bparts, p->nbparts, ctx->stream));
+  UTIL(launch_sumsq_partials(p->b64, p->ncells, p->bparts, p->nbparts, ctx->stream));
   if (p->mode == SIP_MODE_F32) {  // rhs and solution converted to single precision
-    UTIL(launch_cast_f64_f32(p->b64, p->r32, p->nl, ctx->stream));
-    UTIL(launch_cast_f64_f32(p->x64, p->d32, p->nl, ctx->stream));
+    UTIL(launch_cast_f64_f32(p->b64, p->r32, p->ncells, ctx->stream));
+    UTIL(launch_cast_f64_f32(p->x64, p->d32, p->ncells, ctx->stream));
   }
   UTIL(launch_finalize(p->bparts, p->nbparts, p->ctl, p->hist, p->hist_cap, p->status, FIN_BNORM, ctx->stream));
   return SIP_OK;
@@ -552,7 +534,7 @@ int begin_sequence(sip_plan *p, double rtol, int max_iters) {
 
 int end_sequence(sip_plan *p) {
   sip_ctx *ctx = p->ctx;
-  if (p->mode == SIP_MODE_F32) UTIL(launch_cast_f32_f64(p->d32, p->x64, p->nl, ctx->stream));
+  if (p->mode == SIP_MODE_F32) UTIL(launch_cast_f32_f64(p->d32, p->x64, p->ncells, ctx->stream));
   for (auto &bh : p->blocks) UTIL(launch_from_plan_f64(p->x64, bh.d.x, bh.db, ctx->stream));
   CU(cudaMemcpyAsync(&p->h_ctl[2], p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
   int rc = check_status(p);  // synchronises
@@ -568,102 +550,89 @@ std::vector<int> plan_kinds(int mode) {
   return {K_FACTOR32, K_FWD32, K_BWD32, K_BWD32Z};
 }
 
-// Tile shape.  Column tiles are 32 x TK.  The substitution sweeps
-// (sip_psweeps.cuh) run a tile as NW = TK / Q warps of Q rows with a D-stage
-// prefetch ring; the factorisation (sip_factor.cuh) runs it as TK / 2 warps of
-// 2 rows with its own stage depth R.
-//
-// Cost model of a sweep: the critical path of a block walks the tile chain to
-// its last tile and then that tile's walk, (nTJ - 1) 32 + (nTK - 1) TK + nx +
-// 32 + TK - 2 planes at the time of one plane, plus, per hop to the next
-// tile, the face latency between SMs (~0.45 us one-way, measured on GB300)
-// and the start slack.  The time of a plane: in FP64 each sub-partition's
-// FP64 pipe runs 4 Q warp-wide operations of 64 cycles for each of its warps
-// (NW / 4 of them); in FP32 a warp issues ~60 + 25 Q instructions at a few
-// cycles each, two warps per sub-partition overlapping.
+// Tile shape: rows per thread Q and warps NW (tile = 32 x Q*NW), stage depth
+// R.  A sweep's time is (steps on its critical path) x (time of one step).
+// The critical path of a block walks the tile chain to its last tile, each
+// hop lagging by the tile's extent plus the start slack, then that tile's own
+// walk: (nTJ-1)(32 + lead) + (nTK-1)(TK + lead) + nx + 32 + TK - 2 steps.  A
+// step is latency-bound and grows with the warps resident on an SM (they
+// share the SM's load/store pipe): measured on GB300 (256^3 and 128^3
+// Poisson blocks, every shape) as 1 + beta x warps per SM with beta = 0.04
+// for the FP32 sweeps and 0.057 for FP64, and 1.45x longer with four rows per
+// thread than with two at the same TK.  Only shapes whose tiles are all
+// resident at once are taken (else the fewest waves); R = 3 unless forced
+// (deeper rings measured slower on GB300: 3 beat 4 by up to 11 % and 6 is
+// slower still).
 struct ShapeChoice {
-  int TK = 0, Q = 0, NW = 0, D = 0;  // sweeps
-  int fR = 0;                         // factorisation stage depth
-  int ntiles = 0;
-  int cap[K_NKINDS] = {};             // resident CTAs per kind
+  int Q = 0, NW = 0, ntiles = 0;
+  int R[K_NKINDS] = {}, cap[K_NKINDS] = {};
   double score = 1e300;
 };
 
-constexpr double kHopNs = 450.0;  // face word latency between SMs (store to observed load)
-
-double plane_ns(int Q, int NW, bool fp64) {
-  const double per_sp = std::max(1.0, NW / 4.0);  // warps per sub-partition
-  const double cyc = fp64 ? std::max(4.0 * Q * 64.0 * per_sp, 300.0) + 100.0
-                          : (60.0 + 25.0 * Q) * 3.0 * std::max(1.0, per_sp / 1.5);
-  return cyc / 2.07;
-}
-
 std::vector<ShapeChoice> shape_candidates(sip_ctx *ctx, const std::vector<BlockHost> &blocks,
-                                          const std::vector<int> &kinds, int tab_ints, int forceTK, int forceD,
+                                          const std::vector<int> &kinds, int tab_ints, int forceTK, int forceR,
                                           int forceQ, bool fp64) {
+  const double beta = fp64 ? 0.057 : 0.04;
   std::vector<ShapeChoice> all;
-  const int fac = kinds[0];
-  for (int Q : kWQs)
-    for (int D : kWDs)
-      for (int NW = 1; NW <= 8; ++NW) {
-        const int TK = Q * NW;
-        if (forceTK > 0 && TK != forceTK) continue;
-        if (forceQ > 0 && Q != forceQ) continue;
-        if (forceD > 0 && D != forceD) continue;
-        if (TK % 2 != 0 || TK / 2 > 16) continue;  // the factorisation's CTA (TK / 2 warps of 2 rows)
-        ShapeChoice c;
-        c.TK = TK;
-        c.Q = Q;
-        c.NW = NW;
-        c.D = D;
-        bool ok = true;
-        int capmin = INT_MAX;
-        for (size_t q = 1; q < kinds.size() && ok; ++q) {
-          const int kind = kinds[q];
-          const void *f = wkernel_ptr(kind, Q, D);
-          if (!f) { ok = false; break; }
-          const size_t smem = wkernel_smem(kind, Q, D, NW);
-          if (smem + ctx->kernel_static_smem > ctx->smem_optin) { ok = false; break; }
-          c.cap[kind] = ctx->nsm * max_active(f, 32 * NW, smem);
-          if (c.cap[kind] < 1) ok = false;
-          capmin = std::min(capmin, c.cap[kind]);
+  for (int Q : kQs)
+    for (int NW = 1; NW <= 16; ++NW) {
+      const int TK = Q * NW, NT = 32 * NW;
+      if (forceTK > 0 && TK != forceTK) continue;
+      if (forceQ > 0 && Q != forceQ) continue;
+      if (forceQ == 0 && forceTK == 0 && Q != 2) continue;  // 2 rows per thread measured fastest
+      // the model was fitted up to 8 warps per tile; 16 measured slower than
+      // it predicts (384^3 FP64: 32 x 32 tiles 5.85 ms per iteration, 32 x 24
+      // 4.85 ms), so automatic choices stop at 12
+      if (forceTK == 0 && NW > 12) continue;
+      ShapeChoice c;
+      c.Q = Q;
+      c.NW = NW;
+      int capmin = INT_MAX;
+      bool ok = true;
+      for (int kind : kinds) {
+        const bool fac = kind == K_FACTOR || kind == K_FACTOR32;
+        int bR = 0, bcap = 0;
+        for (int R : {3, 4, 6, 2}) {
+          // the one-off factorisation may drop to a 2-stage ring when its
+          // 64-byte input records do not fit a wide tile
+          if (R == 2 ? !fac : (forceR > 0 && R != forceR)) continue;
+          if (R == 2 && bcap > 0) break;
+          const size_t smem = kernel_smem(kind, Q, R, NT, tab_ints);
+          if (smem + ctx->kernel_static_smem > ctx->smem_optin) continue;
+          const int capk = ctx->nsm * max_active(kernel_ptr(kind, Q, R), NT, smem);
+          if (capk > bcap) { bR = R; bcap = capk; }
+          if (forceR == 0 && capk > 0 && R == 3) break;  // R = 3 when it fits
         }
-        if (!ok) continue;
-        {  // factorisation: 2 rows per thread, TK / 2 warps, deepest ring that fits (3 preferred)
-          const int NT = 32 * (TK / 2);
-          int bR = 0, bcap = 0;
-          for (int R : {3, 4, 6, 2}) {
-            const size_t smem = kernel_smem(fac, 2, R, NT, tab_ints);
-            if (smem + ctx->kernel_static_smem > ctx->smem_optin) continue;
-            const int capk = ctx->nsm * max_active(kernel_ptr(fac, 2, R), NT, smem);
-            if (capk > bcap) { bR = R; bcap = capk; }
-            if (capk > 0 && R == 3) break;
-          }
-          if (bcap < 1) continue;
-          c.fR = bR;
-          c.cap[fac] = bcap;
-        }
-        const double tau = plane_ns(Q, NW, fp64);
-        double path_ns = 0;
-        for (auto &bh : blocks) {
-          const int nTJ = (bh.d.ny + kTJ - 1) / kTJ, nTK = (bh.d.nz + TK - 1) / TK;
-          c.ntiles += nTJ * nTK;
-          const double planes = (double)(nTJ - 1) * kTJ + (double)(nTK - 1) * TK + bh.d.nx + kTJ + TK - 2;
-          path_ns = std::max(path_ns, planes * tau + (double)(nTJ - 1 + nTK - 1) * (kHopNs + 3.0 * tau));
-        }
-        // tiles beyond the resident CTAs wait for a CTA to finish one; a
-        // deeper ring is preferred on ties
-        const double waves = std::ceil((double)c.ntiles / std::max(1, capmin));
-        c.score = path_ns * (waves > 1 ? 1.0 + 0.25 * (waves - 1) : 1.0) * (D == 8 ? 1.0 : 1.05);
-        all.push_back(c);
+        if (bcap < 1) { ok = false; break; }
+        c.R[kind] = bR;
+        c.cap[kind] = bcap;
+        capmin = std::min(capmin, bcap);
       }
+      if (!ok) continue;
+      long long steps = 0;
+      for (auto &bh : blocks) {
+        const int nTJ = (bh.d.ny + kTJ - 1) / kTJ, nTK = (bh.d.nz + TK - 1) / TK;
+        c.ntiles += nTJ * nTK;
+        const int R = c.R[kinds[1]];
+        // hop slack of the fitted model (the per-step factor beta was fitted with it)
+        const int lead = std::min(R + 1, std::max(bh.d.nx - 1, 0));
+        steps = std::max(steps, (long long)(nTJ - 1) * (kTJ + lead) + (long long)(nTK - 1) * (TK + lead) +
+                                    bh.d.nx + kTJ + TK - 2);
+      }
+      const int waves = (c.ntiles + capmin - 1) / capmin;
+      // warps per SM, averaged: a few SMs holding a second tile cost a little
+      const double per_sm = (double)NW * std::max(1.0, (double)c.ntiles / ctx->nsm);
+      // four rows per thread: measured 1.45x the step time of two at equal TK
+      c.score = (double)steps * (1.0 + beta * per_sm) * (Q == 4 ? 1.45 : 1.0) * waves * (waves > 1 ? 4.0 : 1.0);
+      all.push_back(c);
+    }
   std::stable_sort(all.begin(), all.end(), [](const ShapeChoice &a, const ShapeChoice &b) { return a.score < b.score; });
   return all;
 }
 
 ShapeChoice choose_shape(sip_ctx *ctx, const std::vector<BlockHost> &blocks, const std::vector<int> &kinds,
-                         int tab_ints, int forceTK, int forceD, int forceQ, bool fp64) {
-  const std::vector<ShapeChoice> c = shape_candidates(ctx, blocks, kinds, tab_ints, forceTK, forceD, forceQ, fp64);
+                         int tab_ints, int forceTK, int forceR, int forceQ, bool fp64) {
+  const std::vector<ShapeChoice> c = shape_candidates(ctx, blocks, kinds, tab_ints, forceTK, forceR, forceQ, fp64);
   return c.empty() ? ShapeChoice() : c.front();
 }
 
@@ -733,12 +702,12 @@ double time_sweeps(sip_plan *p) {
   cudaStream_t st = ctx->stream;
   const bool f64 = p->mode == SIP_MODE_F64;
   if (f64) {
-    if (cudaMemsetAsync(p->y64, 0, (size_t)p->nl * 8, st) != cudaSuccess) return -1;
-  } else if (cudaMemsetAsync(p->y32, 0, (size_t)p->nl * 4, st) != cudaSuccess ||
-             cudaMemsetAsync(p->d32, 0, (size_t)p->nl * 4, st) != cudaSuccess) {
+    if (cudaMemsetAsync(p->y64, 0, (size_t)p->ncells * 8, st) != cudaSuccess) return -1;
+  } else if (cudaMemsetAsync(p->y32, 0, (size_t)p->ncells * 4, st) != cudaSuccess ||
+             cudaMemsetAsync(p->d32, 0, (size_t)p->ncells * 4, st) != cudaSuccess) {
     return -1;
   }
-  if (cudaMemsetAsync(p->x64, 0, (size_t)p->nl * 8, st) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(p->x64, 0, (size_t)p->ncells * 8, st) != cudaSuccess) return -1;
   if (cudaMemsetAsync(p->tickets, 0, 4 * sizeof(int), st) != cudaSuccess) return -1;
   if (launch_set_ctl(p->ctl, -1.0, 0, st) != cudaSuccess) return -1;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -841,24 +810,6 @@ int sip_create(sip_ctx **out, int device, void *stream) {
         }
         ctx->kernel_static_smem = std::max(ctx->kernel_static_smem, (size_t)fa.sharedSizeBytes);
       }
-  for (int kind = 0; kind < K_NKINDS; ++kind)
-    for (int Q : kWQs)
-      for (int D : kWDs) {
-        const void *f = wkernel_ptr(kind, Q, D);
-        if (!f) continue;
-        cudaFuncAttributes fa;
-        cudaError_t e = cudaFuncGetAttributes(&fa, f);
-        if (e == cudaSuccess)
-          e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(ctx->smem_optin - fa.sharedSizeBytes));
-        if (e != cudaSuccess) {
-          g_create_error = std::string("kernel attribute setup: ") + cudaGetErrorString(e);
-          if (ctx->mempool) cudaMemPoolDestroy(ctx->mempool);
-          delete ctx;
-          return SIP_ERR_CUDA;
-        }
-        ctx->kernel_static_smem = std::max(ctx->kernel_static_smem, (size_t)fa.sharedSizeBytes);
-      }
   *out = ctx;
   return SIP_OK;
 }
@@ -946,16 +897,12 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     }
   }
   if (opt.tile_j != 0 && opt.tile_j != kTJ) return fail(ctx, SIP_ERR_INVALID_ARG, "tile_j must be 0 or 32");
-  if (opt.tile_k < 0 || opt.tile_k > 32 || (opt.tile_k > 0 && opt.tile_k % 2 != 0))
-    return fail(ctx, SIP_ERR_INVALID_ARG, "tile_k must be 0 (auto) or an even number <= 32");
-  if (opt.stages != 0 && opt.stages != 4 && opt.stages != 8)
-    return fail(ctx, SIP_ERR_INVALID_ARG, "stages must be 0 (auto), 4 or 8");
-  if (opt.rows_per_thread != 0 && opt.rows_per_thread != 1 && opt.rows_per_thread != 2 && opt.rows_per_thread != 4 &&
-      opt.rows_per_thread != 8)
-    return fail(ctx, SIP_ERR_INVALID_ARG, "rows_per_thread must be 0 (auto), 1, 2, 4 or 8");
-  if (opt.rows_per_thread > 0 && opt.tile_k > 0 &&
-      (opt.tile_k % opt.rows_per_thread != 0 || opt.tile_k / opt.rows_per_thread > 8))
-    return fail(ctx, SIP_ERR_INVALID_ARG, "tile_k must be rows_per_thread times 1..8 warps");
+  if (opt.tile_k < 0 || opt.tile_k > 64 || (opt.tile_k > 0 && opt.tile_k % 2 != 0))
+    return fail(ctx, SIP_ERR_INVALID_ARG, "tile_k must be 0 (auto) or an even number <= 64");
+  if (opt.stages != 0 && opt.stages != 3 && opt.stages != 4 && opt.stages != 6)
+    return fail(ctx, SIP_ERR_INVALID_ARG, "stages must be 0 (auto), 3, 4 or 6");
+  if (opt.rows_per_thread != 0 && opt.rows_per_thread != 2 && opt.rows_per_thread != 4)
+    return fail(ctx, SIP_ERR_INVALID_ARG, "rows_per_thread must be 0 (auto), 2 or 4");
   if (opt.autotune != 0 && opt.autotune != 1) return fail(ctx, SIP_ERR_INVALID_ARG, "autotune must be 0 or 1");
   if (opt.autotune && opt.tile_k == 0 && opt.rows_per_thread == 0 && opt.stages == 0) {
     const std::string sig = tune_signature(ctx, blocks, nblocks, opt);
@@ -981,8 +928,8 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     for (const ShapeChoice &c : cand) {
       if (tried == kTuneCandidates) break;
       o.rows_per_thread = c.Q;
-      o.tile_k = c.TK;
-      o.stages = c.D;
+      o.tile_k = c.Q * c.NW;
+      o.stages = c.R[plan_kinds(opt.mode)[1]];
       sip_plan *tp = nullptr;
       last_rc = sip_factor(ctx, blocks, nblocks, ifaces, nifaces, &o, &tp);
       if (last_rc != SIP_OK) {
@@ -1000,7 +947,7 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
       }
     }
     if (!best) return fail(ctx, SIP_ERR_CUDA, "autotune: no candidate shape could be timed");
-    tune_store(sig, best->sQ, best->TK, best->sD, best_ms);
+    tune_store(sig, best->Q, best->TK, best->Rk[plan_kinds(opt.mode)[1]], best_ms);
     best->opt.autotune = 1;
     *out = best;
     return SIP_OK;
@@ -1025,21 +972,16 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
   const std::vector<int> kinds = plan_kinds(p->mode);
   const ShapeChoice sc = choose_shape(ctx, p->blocks, kinds, p->tab_ints, opt.tile_k, opt.stages, opt.rows_per_thread,
                                       p->mode == SIP_MODE_F64);
-  if (sc.TK == 0) {
+  if (sc.Q == 0) {
     delete p;
     return fail(ctx, SIP_ERR_INVALID_ARG, "no tile shape fits on an SM");
   }
-  p->TK = sc.TK;
-  p->Q = 2;  // factorisation: 2 rows per thread, TK / 2 warps
-  p->NW = sc.TK / 2;
-  p->NT = 32 * p->NW;
-  p->sQ = sc.Q;
-  p->sNWT = sc.NW;
-  p->sD = sc.D;
-  p->Rk[kinds[0]] = sc.fR;
-  p->lead = 3;
-  if (const char *e = getenv("SIP_SWEEP_LEAD")) p->lead = std::max(0, atoi(e));
+  p->Q = sc.Q;
+  p->NW = sc.NW;
+  p->NT = 32 * sc.NW;
+  p->TK = sc.Q * sc.NW;
   for (int k : kinds) {
+    p->Rk[k] = sc.R[k];
     p->gridk[k] = sc.cap[k];
   }
 
@@ -1062,16 +1004,11 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     db.cell0 = cell0;
     db.PO = db.F = nullptr;
     db.face0 = face0;
-    // room for the factorisation's 6-word records (the sweeps need 2 per value)
     db.face_tile_words = (long long)db.nsteps_max * (kTJ + p->TK) * kFaceWordsMax;
     db.lo_blk = db.hi_blk = -1;
     db.lo_nj = db.lo_nk = db.hi_nj = db.hi_nk = 0;
-    db.row0 = p->nrows;  // the residual kernel's tasks: one position of a tile-layout row each
-    db.Lp = db.nx + kTJ - 1;
-    db.sk0 = p->nl;
-    db.pad_ = 0;
-    p->nl += (long long)db.nz * db.nTJ * db.Lp * kTJ;
-    p->nrows += (long long)db.nz * db.nTJ * db.Lp;
+    db.row0 = p->nrows;
+    p->nrows += (long long)db.nz * (db.nx + db.ny - 1);
     const int nt = db.nTJ * db.nTK;
     p->ntiles += nt;
     face0 += (long long)nt * db.face_tile_words;
@@ -1103,14 +1040,6 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
   do {                                                   \
     cudaError_t e_ = palloc(p, &(ptr), (size_t)(count)); \
     if (e_ != cudaSuccess) return bail(e_, #ptr);        \
-  } while (0)
-  // tile-layout arrays: NL elements of `width` values between two margins
-  // of kColMargin elements; ptr points at element 0
-#define PAC(ptr, width)                                                                  \
-  do {                                                                                   \
-    cudaError_t e_ = palloc(p, &(ptr), (size_t)(p->nl + 2 * kColMargin) * (width));      \
-    if (e_ != cudaSuccess) return bail(e_, #ptr);                                        \
-    (ptr) += kColMargin * (width);                                                       \
   } while (0)
   const long long N = ncells;
   const bool f64 = p->mode == SIP_MODE_F64;
@@ -1147,36 +1076,32 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     PA(p->trace, (size_t)K_NKINDS * p->ntiles * kTraceWords);
     cudaMemsetAsync(p->trace, 0, (size_t)K_NKINDS * p->ntiles * kTraceWords * 8, ctx->stream);
   }
-  // vectors and records in the tile layout (NL elements: cells plus
-  // padding, which stays zero); the factorisation input a7 in the plane
-  // layout (N cells)
-  const long long NL = p->nl;
-  PAC(p->b64, 1);
-  PAC(p->x64, 1);
+  PA(p->b64, N);
+  PA(p->x64, N);
   double *a7 = nullptr;
   PA(a7, N * 8);
   const int na = a_rec_values(sym);
   if (f64) {
     double *rf = nullptr, *rb = nullptr, *ra = nullptr;
-    PAC(rf, 4);
-    PAC(rb, 4);
-    PAC(ra, na);
+    PA(rf, N * 4);
+    PA(rb, N * 4);
+    PA(ra, N * na);
     p->recF = rf;
     p->recB = rb;
     p->recA = ra;
-    PAC(p->y64, 1);
+    PA(p->y64, N);
   } else {
     float *rf = nullptr, *rb = nullptr, *ra = nullptr;
-    PAC(rf, 4);
-    PAC(rb, 4);
-    PAC(ra, na);
+    PA(rf, N * 4);
+    PA(rb, N * 4);
+    PA(ra, N * na);
     p->recF = rf;
     p->recB = rb;
     p->recA = ra;
-    PAC(p->r32, 1);
-    PAC(p->d32, 1);
-    PAC(p->y32, 1);
-    if (!p->a32in && p->mode == SIP_MODE_F32_REFINED) PAC(p->arec64, na);
+    PA(p->r32, N);
+    PA(p->d32, N);
+    PA(p->y32, N);
+    if (!p->a32in && p->mode == SIP_MODE_F32_REFINED) PA(p->arec64, N * na);
   }
   pool_keep_peak(ctx);
   {
@@ -1192,8 +1117,12 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
   if (nifaces > 0) {
     // one entry per interface face cell, couplings in interface order (lo side first)
     std::vector<int> at_cell;  // entry of a plan cell, -1 if none
-    at_cell.assign((size_t)p->nl, -1);
-    auto cell_of = [&](int b, int i, int j, int k) { return tile_elem(p->blocks[b].db, i, j, k); };
+    at_cell.assign((size_t)ncells, -1);
+    auto cell_of = [&](int b, int i, int j, int k) {
+      const BlockHost &bh = p->blocks[b];
+      return p->blocks[b].db.cell0 +
+             plane_row_base(bh.PO.data(), bh.F.data(), bh.d.nx + bh.d.ny - 2, bh.d.nx, i + j + k, k) + j;
+    };
     auto add = [&](long long cell, long long nb, const void *src, long long pn) {
       int &e = at_cell[(size_t)cell];
       if (e < 0) {
@@ -1218,7 +1147,7 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     }
     p->nhalo = (int)hents.size();
     HaloSrc *dsrc = nullptr;
-    PAC(p->beff64, 1);
+    PA(p->beff64, N);
     PA(p->halo, p->nhalo);
     PA(dsrc, hsrcs.size());
     cudaError_t e = cudaMemcpyAsync(p->halo, hents.data(), hents.size() * sizeof(HaloEntry),
@@ -1252,19 +1181,8 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->tickets, 0, 4 * sizeof(int), st);
     const size_t es = f64 ? 8 : 4;
-    // the tile layout's padding and margins hold zero records and values
-    auto zero_col = [&](const void *ptr, int width, size_t es_) {
-      if (e != cudaSuccess || !ptr) return;
-      const unsigned char *b0 = static_cast<const unsigned char *>(ptr) - kColMargin * width * es_;
-      e = cudaMemsetAsync((void *)b0, 0, (size_t)(NL + 2 * kColMargin) * width * es_, st);
-    };
-    zero_col(p->recF, 4, es);
-    zero_col(p->recB, 4, es);
-    zero_col(p->recA, na, es);
-    zero_col(p->arec64, na, 8);
-    for (const void *v : {(const void *)p->b64, (const void *)p->x64, (const void *)p->y64, (const void *)p->beff64})
-      zero_col(v, 1, 8);
-    for (const void *v : {(const void *)p->r32, (const void *)p->d32, (const void *)p->y32}) zero_col(v, 1, 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->recF, 0, (size_t)N * 4 * es, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->recB, 0, (size_t)N * 4 * es, st);
     // host vectors must outlive the async copies
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bail(e, "plan upload");
@@ -1556,9 +1474,9 @@ const char *sip_kernel_name(int kind) {
 
 int sip_plan_shape(sip_plan *p, int *rows_per_thread, int *tile_k, int *stages) {
   if (!p) return SIP_ERR_INVALID_ARG;
-  if (rows_per_thread) *rows_per_thread = p->sQ;
+  if (rows_per_thread) *rows_per_thread = p->Q;
   if (tile_k) *tile_k = p->TK;
-  if (stages) *stages = p->sD;
+  if (stages) *stages = p->Rk[plan_kinds(p->mode)[1]];
   return SIP_OK;
 }
 
@@ -1584,8 +1502,8 @@ int sip_plan_destroy(sip_plan *p) {
                 const int gt = bh.db.tile0 + ck * bh.db.nTJ + cj;
                 const unsigned long long *r = &h[((size_t)k * p->ntiles + gt) * kTraceWords];
                 if (!r[0]) continue;
-                fprintf(fo, "%s %d %d %d %llu %llu %llu %llu %llu %llu %llu %llu\n", sip_kernel_name(k), gt, cj, ck,
-                        r[0], r[1], r[2], r[3], r[4], r[5], r[6], r[7]);
+                fprintf(fo, "%s %d %d %d %llu %llu %llu %llu %llu %llu\n", sip_kernel_name(k), gt, cj, ck, r[0], r[1],
+                        r[2], r[3], r[4], r[5]);
               }
         fclose(fo);
       }

@@ -18,7 +18,7 @@ namespace sipk {
 // (each group of three quotients takes one FP64 division: LB, LW, LS through
 // 1/(dB dW dS), the U entries through 1/LP; FP64 throughput bounds the steps).
 // Arithmetic in FP64; stored (as TF) into the L record [LB LW LS 1/LP] and
-// the U record [UE UN UT 0] of the plan's tile layout.  Faces carry (UN, UE, UT): 48 bytes.
+// the U record [UE UN UT 0].  Faces carry (UN, UE, UT): 48 bytes.
 template <typename TF, int Q, int R>
 __global__ void __launch_bounds__(512) k_factor(FacParams<TF> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(512) k_factor(FacParams<TF> P) {
           hK[2] = Face<double>::get(wv + 4);
         }
       }
+      __syncwarp();  // the face wait above diverges the warp: reconverge before the CTA barrier
       __syncthreads();
       double nUN[Q], nUE[Q], nUT[Q];
 #pragma unroll
@@ -181,8 +182,7 @@ __global__ void __launch_bounds__(512) k_factor(FacParams<TF> P) {
           if (LP == 0.0 || !isfinite(RLP) || !isfinite(LB) || !isfinite(LW) || !isfinite(LS) ||
               !isfinite(UN) || !isfinite(UE) || !isfinite(UT) || !isfinite(LP))
             atomicCAS(c.status, DEV_OK, DEV_BREAKDOWN);
-          // records in the plan's tile layout (the input a7 is in the plane layout)
-          const long long cell = tile_elem(B, i, g.j, g.k(q));
+          const long long cell = B.cell0 + rb(g.s0 + t, g.k(q)) + g.j;
           TF *fr = P.recF + cell * 4;
           fr[REC_LB] = (TF)LB;
           fr[REC_LW] = (TF)LW;

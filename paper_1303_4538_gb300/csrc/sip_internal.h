@@ -51,31 +51,7 @@ struct DevBlock {
   // rows of the row-parallel kernels: the block's plane rows (s, k) are
   // numbered row0 + k (nx + ny - 1) + (s - k)
   long long row0;
-  // Tile layout of the plan's vectors and records: for each 32-wide block of
-  // columns cj = j / 32 and each row k, an array of Lp = nx + 31 positions x
-  // 32 lanes, position ps = i + (j mod 32) holding cell (i, j, k) in lane
-  // j mod 32.  A plane s = i + j + k is position s - (32 cj + k) of every
-  // array, so the 32 lanes of a tile row at one plane are contiguous, and one
-  // plane further is 32 elements on.  Cell (i, j, k) is element
-  //   sk0 + ((k nTJ + cj) Lp + i + (j mod 32)) 32 + (j mod 32);
-  // elements at other positions or lanes (outside 0 <= i < nx, j < ny) are
-  // padding holding zeros.
-  long long sk0;
-  int Lp;
-  int pad_;
 };
-
-__host__ __device__ inline long long tile_elem(const DevBlock &B, int i, int j, int k) {
-  const int l = j & 31;
-  return B.sk0 + (((long long)k * B.nTJ + (j >> 5)) * B.Lp + i + l) * 32 + l;
-}
-
-// Every tile-layout array of a plan has kColMargin zero elements before its
-// first and after its last element, so a sweep's copy addresses (which run
-// up to TK + D positions, 32 elements each, past an array's ends at the
-// plan's edges) always lie in the allocation; copies of cells outside the
-// block are zero-filled by size, not by address.
-constexpr long long kColMargin = 2048;
 
 __host__ __device__ inline int plane_row_base(const int *PO, const int *F, int mmax, int nx, int s, int k) {
   const int m = s - k;
@@ -122,24 +98,26 @@ struct SweepCommon {
   uint64_t *faces;
   int *status;
   long long max_spin;
-  int lead;  // start slack of the warp-decoupled sweeps, in steps
   // diagnostics (nullable): per tile [claim, gate passed, end, slow face waits,
-  // ns in slow waits, SM id, slow warp-ring waits, ns in them]; globaltimer
-  // nanoseconds
+  // ns in slow waits, SM id]; globaltimer nanoseconds
   unsigned long long *trace;
 };
-constexpr int kTraceWords = 8;
+constexpr int kTraceWords = 6;
 
-// Substitution sweep parameters (forward: rec = L records, sa = r, out = y
-// (may alias r); backward: rec = U records, sa = y, sb = x (unused when x = 0
-// on entry), out = x); all in the plan's column layout.
 template <typename T>
-struct WParams {
+struct FwdParams {
   SweepCommon c;
-  const T *rec;
-  const T *sa;
-  const T *sb;
-  T *out;
+  const T *rec;  // L records
+  const T *r;    // right-hand side of the substitution (the residual)
+  T *y;          // may alias r
+};
+
+template <typename T>
+struct BwdParams {
+  SweepCommon c;
+  const T *rec;  // backward records
+  const T *y;
+  T *x;          // correction accumulated in place (x <- x + d)
 };
 
 template <typename TF>
@@ -218,7 +196,7 @@ cudaError_t launch_resnorm(const NatBlock &nb, double *scratch, double *out2, cu
 constexpr int kNoallocParts = 16384;
 constexpr int kNoallocMaxDevices = 64;
 cudaError_t noalloc_scratch(int device, double **out);
-// drop the cached address of `device` (after a failed launch)
+// drops the cached address of `device` (after a failed launch)
 void noalloc_forget(int device);
 
 // x-interface coupling of a multi-block plan (lagged block Jacobi): every

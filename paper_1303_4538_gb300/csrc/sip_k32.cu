@@ -1,14 +1,22 @@
-// sip_k32.cu -- instantiations of Stone's factorisation (FP64 arithmetic)
-// with FP32 factors, for the mixed-precision refinement and the pure
-// single-precision relaxation.
+// sip_k32.cu -- instantiations of the FP32 sweep kernels (factorisation with
+// FP32 factors, inner iterations of the mixed-precision refinement and the
+// pure single-precision relaxation).
 #include "sip_kernels.h"
 #include "sip_factor.cuh"
+#include "sip_sweeps.cuh"
 
 namespace sipk {
 
 template <int Q, int R>
 static const void *pick32(int kind) {
-  return kind == K_FACTOR32 ? (const void *)k_factor<float, Q, R> : nullptr;
+  if constexpr (R == 2) return kind == K_FACTOR32 ? (const void *)k_factor<float, Q, R> : nullptr;
+  switch (kind) {
+    case K_FACTOR32: return (const void *)k_factor<float, Q, R>;
+    case K_FWD32: return (const void *)k_forward<float, Q, R>;
+    case K_BWD32: return (const void *)k_backward<float, false, Q, R>;
+    case K_BWD32Z: return (const void *)k_backward<float, true, Q, R>;
+    default: return nullptr;
+  }
 }
 
 const void *kernel_ptr_32(int kind, int Q, int R) {

@@ -1,12 +1,20 @@
-// sip_k64.cu -- instantiations of Stone's factorisation with FP64 factors.
+// sip_k64.cu -- instantiations of the FP64 sweep kernels (factorisation with
+// FP64 factors, FP64 forward / backward substitution).
 #include "sip_kernels.h"
 #include "sip_factor.cuh"
+#include "sip_sweeps.cuh"
 
 namespace sipk {
 
 template <int Q, int R>
 static const void *pick64(int kind) {
-  return kind == K_FACTOR ? (const void *)k_factor<double, Q, R> : nullptr;
+  if constexpr (R == 2) return kind == K_FACTOR ? (const void *)k_factor<double, Q, R> : nullptr;
+  switch (kind) {
+    case K_FACTOR: return (const void *)k_factor<double, Q, R>;
+    case K_FWD64: return (const void *)k_forward<double, Q, R>;
+    case K_BWD64: return (const void *)k_backward<double, false, Q, R>;
+    default: return nullptr;
+  }
 }
 
 const void *kernel_ptr_64(int kind, int Q, int R) {

@@ -35,14 +35,4 @@ size_t kernel_smem(int kind, int Q, int R, int nthreads, int tab_ints);
 const void *kernel_ptr_64(int kind, int Q, int R);
 const void *kernel_ptr_32(int kind, int Q, int R);
 
-// Substitution sweeps over the column layout (sip_psweeps.cuh): K_FWD64,
-// K_BWD64, K_FWD32, K_BWD32, K_BWD32Z addressed by rows per warp Q and stage
-// depth D; a CTA of NW warps walks a 32 x (NW Q) tile.
-constexpr int kWQs[3] = {1, 2, 4};
-constexpr int kWDs[2] = {4, 8};
-const void *wkernel_ptr(int kind, int Q, int D);
-size_t wkernel_smem(int kind, int Q, int D, int NW);
-const void *wkernel_ptr_64(int kind, int Q, int D);
-const void *wkernel_ptr_32(int kind, int Q, int D);
-
 }  // namespace sipk

@@ -3,25 +3,21 @@
 // outside the wavefront.
 //
 // The residual has no recurrence, so it does not belong on the critical path
-// of the forward substitution: a kernel over the plan's tile layout computes
-// it ahead of the sweep, and the forward sweep then runs only the L
-// recurrence on r (in place).  In the tile layout (sip_internal.h) the 32
-// lanes l = j & 31 of a j block cj and row k sit side by side at each
-// position p = i + l of the row, so a position is one 32-element run:
-//   element(i, j, k) = row(cj, k) + 32 (i + l) + l,
-//   row(cj, k) = sk0 + 32 (k nTJ + cj) Lp.
-// Work decomposition: one warp per position of a row, lane l = cell
-// (p - l, 32 cj + l, k), so every access of a warp is a contiguous run.  The
-// neighbours of element e are W/E: e -+ 32; S: e - 33 (lane 0: lane 31 of
-// the j block cj - 1 at position p + 31); N: e + 33 (lane 31: lane 0 of
-// cj + 1 at position p - 31); B/T: e -+ 32 nTJ Lp.  Tasks are numbered per
-// block row-major (task = row0 + (k nTJ + cj) Lp + p), so a warp's
-// neighbour rows are read by nearby warps of the same pass and served from
-// L2.  Padding positions (p - l outside [0, nx), or j >= ny) are skipped and
-// keep the zero they were allocated with.
+// of the forward substitution: a row-parallel kernel computes it over the
+// plane layout ahead of the sweep, and the forward sweep then runs only the
+// L recurrence on r (in place).  Work
+// decomposition: one warp per plane row (s, k) of a block; lanes walk the
+// row's cells j (contiguous in memory).  Cell (i, j, k) of row (s, k),
+// m = s - k, sits at rowbase(s, k) + j, and its neighbours are
+//   W (i-1): rowbase(s-1, k) + j      S (j-1): rowbase(s-1, k) + j - 1
+//   E (i+1): rowbase(s+1, k) + j      N (j+1): rowbase(s+1, k) + j + 1
+//   B (k-1): rowbase(s-1, k-1) + j    T (k+1): rowbase(s+1, k+1) + j
+// so every access of a warp is a contiguous run.  Rows are numbered per
+// block k-major (row = row0 + k (nx + ny - 1) + m), which puts the rows a
+// row reads from within one grid-stride pass: they are served from L2.
 //
 // For a symmetric matrix (Eq. 2 with AW_P = AE_W, AS_P = AN_S, AB_P = AT_B)
-// the lower coefficients come from the W, S and B cells' A records.  The
+// the lower coefficients come from the W, S and B cells' A parts.  The
 // seven products are accumulated in the fixed order P, W, E, S, N, B, T
 // with fused multiply-adds; neighbours outside the block contribute zero.
 // The norm is a per-CTA sum of r^2 over a plan-constant grid, so it is
@@ -53,61 +49,80 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_resrow(RowParams<TA, TX, TR>
   const int lane = threadIdx.x & 31;
   const long long nwarps = (long long)gridDim.x * (kRowThreads / 32);
   int bi = -1;
-  int nx = 0, ny = 0, nz = 0, nTJ = 1, Lp = 1;
-  long long task0 = 0, taskend = 0, sk0 = 0, kstr = 0;
+  int nx = 0, ny = 0, nz = 0, mmax = 0, nm = 1;
+  long long row0 = 0, rowend = 0;
+  const int *PO = nullptr, *F = nullptr;
+  // the current block's arrays (block-local cell offsets fit in 32 bits)
+  const TA *__restrict__ Ab = nullptr;
+  const TX *__restrict__ Xb = nullptr;
+  const TX *__restrict__ Bb = nullptr;
+  TR *__restrict__ Rb = nullptr;
   double acc = 0.0;
-  for (long long task = (long long)blockIdx.x * (kRowThreads / 32) + (threadIdx.x >> 5); task < P.nrows;
-       task += nwarps) {
-    while (task >= taskend) {  // tasks ascend: the owning block only moves forward
+  for (long long row = (long long)blockIdx.x * (kRowThreads / 32) + (threadIdx.x >> 5); row < P.nrows;
+       row += nwarps) {
+    while (row >= rowend) {  // rows ascend: the owning block only moves forward
       ++bi;
       const DevBlock &B = P.blocks[bi];
-      nx = B.nx; ny = B.ny; nz = B.nz; nTJ = B.nTJ; Lp = B.Lp;
-      task0 = B.row0;
-      taskend = task0 + (long long)nz * nTJ * Lp;
-      sk0 = B.sk0;
-      kstr = 32ll * nTJ * Lp;
+      nx = B.nx; ny = B.ny; nz = B.nz; mmax = B.mmax; nm = nx + ny - 1;
+      row0 = B.row0; rowend = row0 + (long long)nz * nm;
+      PO = B.PO; F = B.F;
+      Ab = P.arec + B.cell0 * NA;
+      Xb = P.x + B.cell0;
+      Bb = P.b + B.cell0;
+      Rb = P.r + B.cell0;
     }
-    const long long lt = task - task0;
-    const long long rw = lt / Lp;  // row index k nTJ + cj
-    const int ps = (int)(lt - rw * Lp);
-    const int k = (int)(rw / nTJ), cj = (int)(rw - (long long)k * nTJ);
-    const int j = cj * 32 + lane, i = ps - lane;
-    if (j >= ny || (unsigned)i >= (unsigned)nx) continue;
-    const long long c = sk0 + (rw * Lp + ps) * 32 + lane;
-    const bool hw = i > 0, he = i < nx - 1, hs = j > 0, hn = j < ny - 1, hb = k > 0, ht = k < nz - 1;
-    // S / N across a j-block edge: the adjacent block's edge lane, 31 positions away
-    const long long cS = !hs ? c : (lane > 0 ? c - 33 : c - 32 * Lp + 31 * 32 + 31);
-    const long long cN = !hn ? c : (lane < 31 ? c + 33 : c + 32 * Lp - 31 * 32 - 31);
-    const long long cB = hb ? c - kstr : c, cT = ht ? c + kstr : c;
-    const TA *a = P.arec + c * NA;
-    TC r = (TC)P.b[c];
-    const TC x0 = (TC)P.x[c];
-    const TC xw = hw ? (TC)P.x[c - 32] : TC(0);
-    const TC xe = he ? (TC)P.x[c + 32] : TC(0);
-    const TC xs = hs ? (TC)P.x[cS] : TC(0);
-    const TC xn = hn ? (TC)P.x[cN] : TC(0);
-    const TC xb = hb ? (TC)P.x[cB] : TC(0);
-    const TC xt = ht ? (TC)P.x[cT] : TC(0);
-    const TC ap = (TC)a[0], ae = (TC)a[OAE], an = (TC)a[OAN], at = (TC)a[OAT];
-    TC aw, as, ab;
-    if constexpr (SYM) {
-      aw = hw ? (TC)P.arec[(c - 32) * NA + OAE] : TC(0);
-      as = hs ? (TC)P.arec[cS * NA + OAN] : TC(0);
-      ab = hb ? (TC)P.arec[cB * NA + OAT] : TC(0);
-    } else {
-      aw = (TC)a[1];
-      as = (TC)a[3];
-      ab = (TC)a[5];
+    const int lr = (int)(row - row0);
+    const int k = lr / nm, m = lr - k * nm, s = m + k;
+    const int fm = F[m];
+    const int shift = max(0, m - nx + 1);
+    const int bP = PO[s] + F[min(s, mmax)] - fm - shift;
+    int bW = 0, bE = 0, bB = 0, bT = 0;
+    if (m > 0 || k > 0) {
+      const int lo = PO[s - 1] + F[min(s - 1, mmax)];
+      if (m > 0) bW = lo - F[m - 1] - max(0, m - nx);
+      bB = lo - fm - shift;
     }
-    r = fma(-ap, x0, r);
-    r = fma(-aw, xw, r);
-    r = fma(-ae, xe, r);
-    r = fma(-as, xs, r);
-    r = fma(-an, xn, r);
-    r = fma(-ab, xb, r);
-    r = fma(-at, xt, r);
-    P.r[c] = (TR)r;
-    if constexpr (NORM) acc = fma((double)r, (double)r, acc);
+    if (m < mmax || k < nz - 1) {
+      const int hi = PO[s + 1] + F[min(s + 1, mmax)];
+      if (m < mmax) bE = hi - F[m + 1] - max(0, m - nx + 2);
+      bT = hi - fm - shift;
+    }
+    const int jlo = max(0, m - (nx - 1)), jhi = min(ny - 1, m);
+    const bool hb = k > 0, ht = k < nz - 1;
+    for (int j = jlo + lane; j <= jhi; j += 32) {
+      const int i = m - j;
+      const int c = bP + j;
+      const TA *a = Ab + (size_t)c * NA;
+      TC r = (TC)Bb[c];
+      const TC x0 = (TC)Xb[c];
+      const bool hw = i > 0, he = i < nx - 1, hs = j > 0, hn = j < ny - 1;
+      const TC xw = hw ? (TC)Xb[bW + j] : TC(0);
+      const TC xe = he ? (TC)Xb[bE + j] : TC(0);
+      const TC xs = hs ? (TC)Xb[bW + j - 1] : TC(0);
+      const TC xn = hn ? (TC)Xb[bE + j + 1] : TC(0);
+      const TC xb = hb ? (TC)Xb[bB + j] : TC(0);
+      const TC xt = ht ? (TC)Xb[bT + j] : TC(0);
+      const TC ap = (TC)a[0], ae = (TC)a[OAE], an = (TC)a[OAN], at = (TC)a[OAT];
+      TC aw, as, ab;
+      if constexpr (SYM) {
+        aw = hw ? (TC)Ab[(size_t)(bW + j) * NA + OAE] : TC(0);
+        as = hs ? (TC)Ab[(size_t)(bW + j - 1) * NA + OAN] : TC(0);
+        ab = hb ? (TC)Ab[(size_t)(bB + j) * NA + OAT] : TC(0);
+      } else {
+        aw = (TC)a[1];
+        as = (TC)a[3];
+        ab = (TC)a[5];
+      }
+      r = fma(-ap, x0, r);
+      r = fma(-aw, xw, r);
+      r = fma(-ae, xe, r);
+      r = fma(-as, xs, r);
+      r = fma(-an, xn, r);
+      r = fma(-ab, xb, r);
+      r = fma(-at, xt, r);
+      Rb[c] = (TR)r;
+      if constexpr (NORM) acc = fma((double)r, (double)r, acc);
+    }
   }
   if constexpr (NORM) {
     // fixed shuffle tree, then the warps in order

@@ -1,36 +1,43 @@
-// sip_sweeps.cuh -- wavefront machinery of Stone's SIP over the plane layout,
-// used by the factorisation (lu3d, arXiv:1303.4538 Sec. 1 / Sec. 4.1;
-// sip_factor.cuh) and, for its PTX helpers and face words, by the
-// substitution sweeps over the column layout (sip_psweeps.cuh).
+// sip_sweeps.cuh -- sm_103a kernels of Stone's SIP over the plane layout.
 //
-// The factorisation makes a cell depend on its lower neighbours W, S, B;
-// all cells of one hyperplane i + j + k = s are independent, so it advances
-// plane by plane.  Work decomposition:
+// The recurrences of the method (arXiv:1303.4538, Sec. 1 / Sec. 4.1: lu3d,
+// the substitution part of resforward3d, backward3d) make a cell depend on
+// its lower neighbours W, S, B (factorisation and forward substitution) or on
+// its upper neighbours E, N, T (backward substitution).  The residual part of
+// resforward3d has no recurrence and runs in the row-parallel kernel of
+// sip_resrow.cu.  All cells of one hyperplane i + j + k = s are
+// independent, so the sweeps advance plane by plane.  Work decomposition:
 //
 //   * the (j, k) cross-section of a block is cut into 32 x TK column tiles;
 //     one CTA owns a tile; lane = j, and warp w owns the Q rows
 //     k = k0 + w Q .. k0 + w Q + Q - 1, so a thread walks Q columns along i.
 //     At local step t every cell the CTA touches lies on plane s = t + j0 + k0;
-//   * neighbours of the previous plane: W from the thread's own registers, S
-//     from lane j - 1 by warp shuffles, B from the thread's own neighbouring
-//     row, and across warps through a double-buffered shared-memory exchange
-//     (one barrier per step);
-//   * each cell's input record (A) is staged with cp.async.cg (L2 only) R-1
-//     steps ahead into a ring of shared-memory stages; invalid cells are
-//     zero-filled;
-//   * row addresses of the plane layout come from two small per-block tables
-//     held in shared memory (plane offsets PO and the diagonal prefix sums F);
+//   * neighbours of the previous (next) plane: W/E from the thread's own
+//     registers, S/N from lanes j -+ 1 by warp shuffles, B/T from the
+//     thread's own neighbouring row, and across warps through a
+//     double-buffered shared-memory exchange (one barrier per step);
+//   * each cell's static data (factors, or A for the factorisation) is one
+//     16-byte aligned record, staged with cp.async.cg (L2 only) R-1 steps
+//     ahead into a ring of shared-memory stages together with the cell's
+//     values (r; y and x for the backward sweep); invalid
+//     cells are zero-filled, so the arithmetic runs without branches and
+//     inactive threads produce zeros;
+//   * row addresses come from two small per-block tables held in shared
+//     memory (plane offsets PO and the diagonal prefix sums F);
 //   * between tiles, the recurrence's boundary values travel through "faces":
-//     records of 8-byte words whose upper halves carry the launch's epoch tag.
-//     A producer stores them with st.relaxed.gpu; a consumer prefetches them
-//     with cp.async.cg and accepts a record when every tag matches (each word
-//     is self-validating, so no fence or flag is needed); a stale record is
-//     re-read from L2 with ld.relaxed.gpu until it matches.  Before a tile
-//     starts, one thread waits until the upstream tiles are a few steps ahead
-//     ("slack").  Every wait is bounded (max_spin polls), then the kernel
-//     records DEV_TIMEOUT and runs to the end without waiting;
+//     16-byte records of two 8-byte words whose upper halves carry the
+//     launch's epoch tag.  A producer stores a record with one st.relaxed.gpu;
+//     a consumer prefetches it with cp.async.cg with the step's other data and
+//     accepts it when every tag matches (each word is self-validating, so no
+//     fence or flag is needed); a stale record is re-read from L2 with
+//     ld.relaxed.gpu until it matches.  Before a tile starts, one thread waits
+//     until the upstream tiles are a few steps ahead ("slack"), so prefetched
+//     records are normally valid.  Every wait is bounded (max_spin polls),
+//     then the kernel records DEV_TIMEOUT and runs to the end without waiting;
 //   * CTAs claim tiles with an atomic ticket in a dependency-respecting order,
 //     so a tile only waits for tiles claimed earlier by running CTAs.
+// This file holds the shared machinery and the forward and backward
+// substitutions; the factorisation kernel is in sip_factor.cuh.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -321,6 +328,7 @@ __device__ __forceinline__ void slack_gate(const uint64_t *recJ, const uint64_t 
     if (recK) face_wait<W>(recK, expect, w, c, abort, nullptr);
     if (tr) tr[1] = gtimer();
   }
+  __syncwarp();  // thread 0's wait diverges its warp: reconverge before the CTA barrier
   __syncthreads();
 }
 
@@ -344,6 +352,408 @@ template <typename T, int PJ, int Q>
 __device__ __forceinline__ void face_put(uint64_t *p, const T (&v)[Q], int q, unsigned ep, bool pred) {
   if constexpr (PJ == 2) Face<T>::put2_if(p, v[q], v[q + 1], ep, pred);
   else Face<T>::put_if(p, v[q], ep, pred);
+}
+
+// ============================================================ forward sweep
+// The substitution half of resforward3d: y = L^{-1} r with
+//   y_P = (r_P - LB y_B - LW y_W - LS y_S) * (1/LP),  ascending planes.
+// The residual r = b - A x (and its norm) is computed beforehand by the
+// row-parallel kernel, so the wavefront carries only this recurrence.  r and y
+// may alias (in place): a cell's r is staged before its y is stored, and no
+// other cell reads it.
+//
+// Per step a thread issues the copies of step t + R - 1 (row bases from the
+// warp's row-base chunk, one shuffle per row; the cell offsets are kept in the
+// stage for the store) and computes step t from its stage.
+template <typename T, int Q, int R>
+__global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_claim, s_blk;
+  constexpr int W = 2;
+  constexpr int RBY = 4 * (int)sizeof(T);  // bytes of an L record
+  constexpr int C = 32 / Q;                // steps per row-base chunk
+  constexpr int PJ = face_pair<T, Q>();    // rows per J face record
+  const SweepCommon &c = P.c;
+  const unsigned ep = sweep_prologue(c);
+  if (threadIdx.x == 0) s_blk = -1;
+  // block-uniform exit decision (the status word may change during the launch)
+  if (__syncthreads_or(c.ctl->done || ld_relaxed(c.status) != DEV_OK)) return;
+  const unsigned expect = ep + (c.stall ? 0x40000000u : 0u);
+  const int NT = blockDim.x, tid = threadIdx.x;
+  const SweepLayout L = fwd_layout((int)sizeof(T), Q, R, NT, c.tab_ints);
+  int *sPO = reinterpret_cast<int *>(smem_raw);
+  unsigned char *stage = smem_raw + L.tab;
+  T *exB = reinterpret_cast<T *>(stage + (size_t)R * L.step);  // [2][NW][32]: y of a warp's last row
+  uint64_t *fst = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(exB) + L.exch);
+  const int FS = L.fs;
+  bool abort = false;
+
+  for (;;) {
+    const int m = claim_tile(c, &s_claim);
+    if (m >= c.ntiles) break;
+    const Tile tl = c.tiles[m];
+    const DevBlock B = c.blocks[tl.blk];
+    unsigned long long *tr = c.trace ? c.trace + (size_t)tl.gtile * kTraceWords : nullptr;
+    load_tables(B, tl.blk, sPO, &s_blk);
+    const int *sF = sPO + B.nplanes;
+    const Geo<Q> g(B, tl);
+    const int NW = g.NW, lane = g.lane, w = g.w, TK = g.TK;
+    uint64_t *myf = tile_faces(c, B, tl.gtile);
+    uint64_t *upJ = g.hasS ? tile_faces(c, B, tl.gtile - 1) : myf;
+    uint64_t *upK = g.hasB ? tile_faces(c, B, tl.gtile - B.nTJ) : myf;
+    {
+      const int lead = min(sweep_lead((int)sizeof(T)), B.nx - 1);
+      slack_gate<W>(g.hasS ? faceJ(upJ, B, lead + kTJ - 1, 0, W) : nullptr,
+                    g.hasB ? faceK(upK, B, lead + TK - 1, 0, W) : nullptr, expect, c, abort, tr);
+    }
+    // per-row invariants: cell of row q at local step t is i = t - tlo[q]
+    int tlo[Q];
+    bool colq[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      tlo[q] = lane + g.dk(q);
+      colq[q] = g.col(B, q);
+    }
+    const unsigned nxu = (unsigned)B.nx;
+    const long long kface = (long long)B.nsteps_max * TK * W;  // K faces follow the J faces
+    int chunk = 0, cb = -C;  // row-base chunk of issue steps [cb, cb + C)
+    const int kchunk = g.k0 + w * Q + lane % Q;
+    // the block's arrays (cell offsets inside a block fit in 32 bits; a
+    // record offset, 4 values a cell, is scaled in 64 bits)
+    const T *recb = P.rec + B.cell0 * 4;
+    const T *rb = P.r + B.cell0;
+    T *yb = P.y + B.cell0;
+    // running face pointers: records read by the copies of issue step tt and
+    // written at compute step t (row slot w Q; K slot lane)
+    const uint64_t *fjn = upJ + ((long long)(kTJ - 1) * TK + w * Q) * W;
+    const uint64_t *fkn = upK + kface + ((long long)(TK - 1) * kTJ + lane) * W;
+    uint64_t *pjn = myf + (long long)w * Q * W;
+    uint64_t *pkn = myf + kface + (long long)lane * W;
+
+    auto issue = [&](int tt) {
+      if (tt < g.nsteps) {
+        if (tt - cb >= C) {
+          cb += C;
+          chunk = rowbase_chunk<Q>(B, sPO, sF, g.s0, kchunk, cb + lane / Q, g.nsteps);
+        }
+        const int sl = tt % R;
+        unsigned char *st = stage + (size_t)sl * L.step;
+        T *sr = reinterpret_cast<T *>(st + L.rec) + tid;
+        int *so = reinterpret_cast<int *>(st + L.off) + tid;
+        uint64_t *fs = fst + (size_t)sl * FS * W;
+        // addresses of every row first, then the copies (the copies are
+        // ordered memory operations; keeping them together lets the
+        // address arithmetic of all rows overlap)
+        int off[Q];
+        bool v[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          off[q] = __shfl_sync(0xffffffffu, chunk, (tt - cb) * Q + q) + g.j;
+          v[q] = colq[q] && (unsigned)(tt - tlo[q]) < nxu;
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const int o = v[q] ? off[q] : 0;
+          unsigned char *d = st + ((size_t)q * NT + tid) * RBY;
+          const unsigned char *src = reinterpret_cast<const unsigned char *>(recb + (size_t)o * 4);
+#pragma unroll
+          for (int z = 0; z < RBY / 16; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v[q]);
+          cp_async_zfill<sizeof(T)>(sr + q * NT, rb + o, v[q]);
+          so[q * NT] = off[q];
+        }
+#pragma unroll
+        for (int q = 0; q < Q; q += PJ) {
+          const bool vq = PJ == 2 ? (v[q] || v[q + PJ - 1]) : v[q];
+          cp_async_16_if(fs + (w * Q + q) * W, fjn + q * W, lane == 0 && g.hasS && vq);
+        }
+        if (g.eB)  // warp-uniform
+          cp_async_16_if(fs + (TK + lane) * W, fkn, g.hasB && v[0]);
+        fjn += (long long)TK * W;
+        fkn += (long long)kTJ * W;
+      }
+      cp_async_commit();
+    };
+#pragma unroll
+    for (int tt = 0; tt < R - 1; ++tt) issue(tt);
+
+    T ym1[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) ym1[q] = T(0);
+    for (int t = 0; t < g.nsteps; ++t) {
+      issue(t + R - 1);
+      cp_async_wait<R - 1>();
+      const int sl = t % R;
+      const unsigned char *st = stage + (size_t)sl * L.step;
+      const T *sr = reinterpret_cast<const T *>(st + L.rec) + tid;
+      const int *so = reinterpret_cast<const int *>(st + L.off) + tid;
+      const uint64_t *fs = fst + (size_t)sl * FS * W;
+      T *E = exB + (size_t)(t & 1) * NW * 32;
+      E[w * 32 + lane] = ym1[Q - 1];
+      __syncthreads();
+      // faces of this step: J (lane 0, one record per row, or per row pair
+      // in FP32) and K (warp 0, row 0); a stale staged copy is re-read from
+      // L2 (rare: one warp-uniform branch)
+      bool act[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) act[q] = colq[q] && (unsigned)(t - tlo[q]) < nxu;
+      constexpr int NJ = Q / PJ;
+      bool needJ[NJ];
+      uint64_t jw[NJ][2], kw[2] = {0, 0};
+      bool stale = false;
+#pragma unroll
+      for (int r = 0; r < NJ; ++r) {
+        const int q = r * PJ;
+        needJ[r] = lane == 0 && g.hasS && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]);
+        staged_words(fs + (w * Q + q) * W, jw[r]);
+        stale |= needJ[r] && !rec_ok<2>(jw[r], expect);
+      }
+      const bool needK = g.eB && g.hasB && act[0];
+      if (g.eB) {
+        staged_words(fs + (TK + lane) * W, kw);
+        stale |= needK && !rec_ok<2>(kw, expect);
+      }
+      if (__any_sync(0xffffffffu, stale)) {
+#pragma unroll
+        for (int r = 0; r < NJ; ++r)
+          if (needJ[r] && !rec_ok<2>(jw[r], expect))
+            face_wait<2>(upJ + ((long long)(t + kTJ - 1) * TK + w * Q + r * PJ) * W, expect, jw[r], c, abort, tr);
+        if (needK && !rec_ok<2>(kw, expect))
+          face_wait<2>(upK + kface + ((long long)(t + TK - 1) * kTJ + lane) * W, expect, kw, c, abort, tr);
+      }
+      const T yK = needK ? Face<T>::get(kw) : T(0);
+      T ny[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * RBY);
+        const T r = sr[q * NT];
+        T yS = shfl_up1(ym1[q]);
+        if (lane == 0) yS = (g.hasS && act[q]) ? face_row<T, PJ>(jw[q / PJ], q) : T(0);
+        T yB;
+        if (q > 0) yB = ym1[q > 0 ? q - 1 : 0];
+        else if (w > 0) yB = E[(w - 1) * 32 + lane];
+        else yB = yK;
+        T y = fma(-rec[REC_LB], yB, r);
+        y = fma(-rec[REC_LW], ym1[q], y);
+        y = fma(-rec[REC_LS], yS, y);
+        ny[q] = act[q] ? y * rec[REC_RLP] : T(0);
+      }
+      // stores last: y, then the face records (ordered memory operations)
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        if (act[q]) yb[so[q * NT]] = ny[q];
+#pragma unroll
+      for (int q = 0; q < Q; q += PJ)
+        face_put<T, PJ>(pjn + q * W, ny, q, ep, lane == kTJ - 1 && g.hasN && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]));
+      if (g.eT)  // warp-uniform
+        Face<T>::put_if(pkn, ny[Q - 1], ep, g.hasT && act[Q - 1]);
+      pjn += (long long)TK * W;
+      pkn += (long long)kTJ * W;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) ym1[q] = ny[q];
+    }
+    cp_async_wait<0>();
+    if (tr && threadIdx.x == 0) tr[2] = gtimer();
+    __syncthreads();
+  }
+}
+
+// =========================================================== backward sweep
+// backward3d with the update: d_P = y_P - UE d_E - UN d_N - UT d_T
+// (descending planes), x_P <- x_P + d_P.  ZX: x = 0 on entry (x_P <- d_P).
+// Backward step u processes local plane t = last - u.
+template <typename T, bool ZX, int Q, int R>
+__global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_claim, s_blk;
+  constexpr int W = 2;
+  constexpr int RBY = 4 * (int)sizeof(T);  // bytes of a U record
+  constexpr int C = 32 / Q;
+  constexpr int SY = 0, SX = Q;  // scalar slots
+  constexpr int PJ = face_pair<T, Q>();  // rows per J face record
+  const SweepCommon &c = P.c;
+  const unsigned ep = sweep_prologue(c);
+  if (threadIdx.x == 0) s_blk = -1;
+  // block-uniform exit decision (the status word may change during the launch)
+  if (__syncthreads_or(c.ctl->done || ld_relaxed(c.status) != DEV_OK)) return;
+  const unsigned expect = ep + (c.stall ? 0x40000000u : 0u);
+  const int NT = blockDim.x, tid = threadIdx.x;
+  const SweepLayout L = bwd_layout((int)sizeof(T), ZX, Q, R, NT, c.tab_ints);
+  int *sPO = reinterpret_cast<int *>(smem_raw);
+  unsigned char *stage = smem_raw + L.tab;
+  T *exT = reinterpret_cast<T *>(stage + (size_t)R * L.step);  // [2][NW][32]: d of a warp's first row
+  uint64_t *fst = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(exT) + L.exch);
+  const int FS = L.fs;
+  bool abort = false;
+
+  for (;;) {
+    const int m = claim_tile(c, &s_claim);
+    if (m >= c.ntiles) break;
+    const Tile tl = c.tiles[m];
+    const DevBlock B = c.blocks[tl.blk];
+    unsigned long long *tr = c.trace ? c.trace + (size_t)tl.gtile * kTraceWords : nullptr;
+    load_tables(B, tl.blk, sPO, &s_blk);
+    const int *sF = sPO + B.nplanes;
+    const Geo<Q> g(B, tl);
+    const int NW = g.NW, lane = g.lane, w = g.w, TK = g.TK;
+    uint64_t *myf = tile_faces(c, B, tl.gtile);
+    uint64_t *dnJ = g.hasN ? tile_faces(c, B, tl.gtile + 1) : myf;
+    uint64_t *dnK = g.hasT ? tile_faces(c, B, tl.gtile + B.nTJ) : myf;
+    const int last = g.nsteps - 1;
+    {
+      // the consumer of the last valid row (column) needs, `lead` steps into
+      // the walk, cell i = nx-1-lead, published on the producer's step i + lane
+      const int lead = min(sweep_lead((int)sizeof(T)), B.nx - 1);
+      const int i = B.nx - 1 - lead;
+      // (J records of row pairs sit in the slot of the pair's first row)
+      slack_gate<W>(g.hasN ? faceJ(dnJ, B, i + g.nkt - 1, (g.nkt - 1) / PJ * PJ, W) : nullptr,
+                    g.hasT ? faceK(dnK, B, i + g.njt - 1, g.njt - 1, W) : nullptr, expect, c, abort, tr);
+    }
+    int tlo[Q];
+    bool colq[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      tlo[q] = lane + g.dk(q);
+      colq[q] = g.col(B, q);
+    }
+    const unsigned nxu = (unsigned)B.nx;
+    const long long kface = (long long)B.nsteps_max * TK * W;
+    int chunk = 0, cb = -C;  // row-base chunk of issue steps [cb, cb + C)
+    const int kchunk = g.k0 + w * Q + lane % Q;
+    const T *recb = P.rec + B.cell0 * 4;
+    const T *yb = P.y + B.cell0;
+    T *xb = P.x + B.cell0;
+    // running face pointers (descending planes): the records read by the
+    // copies of issue step uu (plane last - uu) and written at step u
+    const uint64_t *fjn = dnJ + ((long long)(last - (kTJ - 1)) * TK + w * Q) * W;
+    const uint64_t *fkn = dnK + kface + ((long long)(last - (TK - 1)) * kTJ + lane) * W;
+    uint64_t *pjn = myf + ((long long)last * TK + w * Q) * W;
+    uint64_t *pkn = myf + kface + ((long long)last * kTJ + lane) * W;
+
+    auto issue = [&](int uu) {
+      if (uu < g.nsteps) {
+        if (uu - cb >= C) {
+          cb += C;
+          chunk = rowbase_chunk<Q>(B, sPO, sF, g.s0, kchunk, last - (cb + lane / Q), g.nsteps);
+        }
+        const int t = last - uu;
+        const int sl = uu % R;
+        unsigned char *st = stage + (size_t)sl * L.step;
+        T *sc = reinterpret_cast<T *>(st + L.rec) + tid;
+        int *so = reinterpret_cast<int *>(st + L.off) + tid;
+        uint64_t *fs = fst + (size_t)sl * FS * W;
+        int off[Q];
+        bool v[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          off[q] = __shfl_sync(0xffffffffu, chunk, (uu - cb) * Q + q) + g.j;
+          v[q] = colq[q] && (unsigned)(t - tlo[q]) < nxu;
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const int o = v[q] ? off[q] : 0;
+          unsigned char *d = st + ((size_t)q * NT + tid) * RBY;
+          const unsigned char *src = reinterpret_cast<const unsigned char *>(recb + (size_t)o * 4);
+#pragma unroll
+          for (int z = 0; z < RBY / 16; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v[q]);
+          cp_async_zfill<sizeof(T)>(sc + (SY + q) * NT, yb + o, v[q]);
+          if constexpr (!ZX) cp_async_zfill<sizeof(T)>(sc + (SX + q) * NT, xb + o, v[q]);
+          so[q * NT] = off[q];
+        }
+#pragma unroll
+        for (int q = 0; q < Q; q += PJ) {
+          const bool vq = PJ == 2 ? (v[q] || v[q + PJ - 1]) : v[q];
+          cp_async_16_if(fs + (w * Q + q) * W, fjn + q * W, lane == kTJ - 1 && g.hasN && vq);
+        }
+        if (g.eT)  // warp-uniform
+          cp_async_16_if(fs + (TK + lane) * W, fkn, g.hasT && v[Q - 1]);
+        fjn -= (long long)TK * W;
+        fkn -= (long long)kTJ * W;
+      }
+      cp_async_commit();
+    };
+#pragma unroll
+    for (int uu = 0; uu < R - 1; ++uu) issue(uu);
+
+    T dE[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) dE[q] = T(0);
+    for (int u = 0; u < g.nsteps; ++u) {
+      issue(u + R - 1);
+      cp_async_wait<R - 1>();
+      const int sl = u % R;
+      const unsigned char *st = stage + (size_t)sl * L.step;
+      const T *sc = reinterpret_cast<const T *>(st + L.rec) + tid;
+      const int *so = reinterpret_cast<const int *>(st + L.off) + tid;
+      const uint64_t *fs = fst + (size_t)sl * FS * W;
+      const int t = last - u;
+      T *E = exT + (size_t)(u & 1) * NW * 32;
+      E[w * 32 + lane] = dE[0];
+      __syncthreads();
+      // faces of this step: J (lane 31, per row or row pair) and K (last warp, last row)
+      bool act[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) act[q] = colq[q] && (unsigned)(t - tlo[q]) < nxu;
+      constexpr int NJ = Q / PJ;
+      bool needJ[NJ];
+      uint64_t jw[NJ][2], kw[2] = {0, 0};
+      bool stale = false;
+#pragma unroll
+      for (int r = 0; r < NJ; ++r) {
+        const int q = r * PJ;
+        needJ[r] = lane == kTJ - 1 && g.hasN && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]);
+        staged_words(fs + (w * Q + q) * W, jw[r]);
+        stale |= needJ[r] && !rec_ok<2>(jw[r], expect);
+      }
+      const bool needK = g.eT && g.hasT && act[Q - 1];
+      if (g.eT) {
+        staged_words(fs + (TK + lane) * W, kw);
+        stale |= needK && !rec_ok<2>(kw, expect);
+      }
+      if (__any_sync(0xffffffffu, stale)) {
+#pragma unroll
+        for (int r = 0; r < NJ; ++r)
+          if (needJ[r] && !rec_ok<2>(jw[r], expect))
+            face_wait<2>(dnJ + ((long long)(t - (kTJ - 1)) * TK + w * Q + r * PJ) * W, expect, jw[r], c, abort, tr);
+        if (needK && !rec_ok<2>(kw, expect))
+          face_wait<2>(dnK + kface + ((long long)(t - (TK - 1)) * kTJ + lane) * W, expect, kw, c, abort, tr);
+      }
+      const T dK = needK ? Face<T>::get(kw) : T(0);
+      T nd[Q], xv[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * RBY);
+        T dN = shfl_dn1(dE[q]);
+        if (lane == kTJ - 1) dN = (g.hasN && act[q]) ? face_row<T, PJ>(jw[q / PJ], q) : T(0);
+        T dT;
+        if (q < Q - 1) dT = dE[q < Q - 1 ? q + 1 : 0];
+        else if (w < NW - 1) dT = E[(w + 1) * 32 + lane];
+        else dT = dK;
+        T d = fma(-rec[RECB_UE], dE[q], sc[(SY + q) * NT]);
+        d = fma(-rec[RECB_UN], dN, d);
+        d = fma(-rec[RECB_UT], dT, d);
+        T xn = d;
+        if constexpr (!ZX) xn = sc[(SX + q) * NT] + d;
+        xv[q] = xn;
+        nd[q] = act[q] ? d : T(0);
+      }
+      // stores last: the update, then the face records (ordered memory operations)
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        if (act[q]) xb[so[q * NT]] = xv[q];
+#pragma unroll
+      for (int q = 0; q < Q; q += PJ)
+        face_put<T, PJ>(pjn + q * W, nd, q, ep, lane == 0 && g.hasS && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]));
+      if (g.eB)  // warp-uniform
+        Face<T>::put_if(pkn, nd[0], ep, g.hasB && act[0]);
+      pjn -= (long long)TK * W;
+      pkn -= (long long)kTJ * W;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) dE[q] = nd[q];
+    }
+    cp_async_wait<0>();
+    if (tr && threadIdx.x == 0) tr[2] = gtimer();
+    __syncthreads();
+  }
 }
 
 }  // namespace sipk

@@ -20,23 +20,11 @@ size_t kernel_smem(int kind, int Q, int R, int NT, int tab) {
   switch (kind) {
     case K_FACTOR:
     case K_FACTOR32: return fac_layout(Q, R, NT, tab).total;
-    default: return 0;
-  }
-}
-
-const void *wkernel_ptr(int kind, int Q, int D) {
-  const void *p = wkernel_ptr_64(kind, Q, D);
-  if (!p) p = wkernel_ptr_32(kind, Q, D);
-  return p;
-}
-
-size_t wkernel_smem(int kind, int Q, int D, int NW) {
-  switch (kind) {
-    case K_FWD64: return c_layout(8, 1, Q, D, NW).total;
-    case K_BWD64: return c_layout(8, 2, Q, D, NW).total;
-    case K_FWD32: return c_layout(4, 1, Q, D, NW).total;
-    case K_BWD32: return c_layout(4, 2, Q, D, NW).total;
-    case K_BWD32Z: return c_layout(4, 1, Q, D, NW).total;
+    case K_FWD64: return fwd_layout(8, Q, R, NT, tab).total;
+    case K_BWD64: return bwd_layout(8, false, Q, R, NT, tab).total;
+    case K_FWD32: return fwd_layout(4, Q, R, NT, tab).total;
+    case K_BWD32: return bwd_layout(4, false, Q, R, NT, tab).total;
+    case K_BWD32Z: return bwd_layout(4, true, Q, R, NT, tab).total;
     default: return 0;
   }
 }
@@ -49,6 +37,9 @@ static int util_grid(long long n) {
   return (int)g;
 }
 
+__device__ __forceinline__ long long plan_cell(const DevBlock &hb, int i, int j, int k) {
+  return hb.cell0 + plane_row_base(hb.PO, hb.F, hb.mmax, hb.nx, i + j + k, k) + j;
+}
 
 // Walk over a block's natural rows (j, k): one warp per row, lanes stepping
 // along i, so the natural-layout side of every copy is coalesced and the index
@@ -64,8 +55,6 @@ static int walk_grid(const DevBlock &hb) {
   return (int)g;
 }
 
-// f(i, j, k, p, c, e): natural index p, plane-layout cell c (the
-// factorisation's input) and tile-layout element e (every other array).
 template <typename Fn>
 __device__ __forceinline__ void walk_rows(const DevBlock &hb, Fn &&f) {
   const int lane = threadIdx.x & 31;
@@ -74,11 +63,9 @@ __device__ __forceinline__ void walk_rows(const DevBlock &hb, Fn &&f) {
   for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < nrows; r += gridDim.x * wpb) {
     const int k = r / hb.ny, j = r - k * hb.ny;
     const int p0 = r * hb.nx;
-    const int l = j & 31;
-    const long long e0 = hb.sk0 + (((long long)k * hb.nTJ + (j >> 5)) * hb.Lp + l) * 32 + l;
     for (int i = lane; i < hb.nx; i += 32) {
       const long long c = hb.cell0 + plane_row_base(hb.PO, hb.F, hb.mmax, hb.nx, i + j + k, k) + j;
-      f(i, j, k, p0 + i, c, e0 + (long long)i * 32);
+      f(i, j, k, p0 + i, c);
     }
   }
 }
@@ -99,7 +86,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_pack_records(PackSrc S, DevBlo
     if (!a) return 0.0;
     return S.f32 ? (double)static_cast<const float *>(a)[p] : static_cast<const double *>(a)[p];
   };
-  walk_rows(hb, [&](int i, int j, int k, int p, long long c, long long e) {
+  walk_rows(hb, [&](int i, int j, int k, int p, long long c) {
     double v[7];
     v[0] = ld(0, p);
     v[2] = i < hb.nx - 1 ? ld(2, p) : 0.0;
@@ -122,31 +109,31 @@ __global__ void __launch_bounds__(kWalkThreads) k_pack_records(PackSrc S, DevBlo
     if (S.sym) {
       const double r4[4] = {v[0], v[2], v[4], v[6]};
       if constexpr (sizeof(TR) == 4) {
-        reinterpret_cast<float4 *>(recA)[e] = make_float4((float)r4[0], (float)r4[1], (float)r4[2], (float)r4[3]);
+        reinterpret_cast<float4 *>(recA)[c] = make_float4((float)r4[0], (float)r4[1], (float)r4[2], (float)r4[3]);
       } else {
-        double2 *d = reinterpret_cast<double2 *>(recA + e * 4);
+        double2 *d = reinterpret_cast<double2 *>(recA + c * 4);
         d[0] = make_double2(r4[0], r4[1]);
         d[1] = make_double2(r4[2], r4[3]);
       }
       if (arec64) {
-        double2 *d = reinterpret_cast<double2 *>(arec64 + e * 4);
+        double2 *d = reinterpret_cast<double2 *>(arec64 + c * 4);
         d[0] = make_double2(r4[0], r4[1]);
         d[1] = make_double2(r4[2], r4[3]);
       }
     } else {
       if constexpr (sizeof(TR) == 4) {
-        float4 *d = reinterpret_cast<float4 *>(recA + e * 8);
+        float4 *d = reinterpret_cast<float4 *>(recA + c * 8);
         d[0] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
         d[1] = make_float4((float)v[4], (float)v[5], (float)v[6], 0.0f);
       } else {
-        double2 *d = reinterpret_cast<double2 *>(recA + e * 8);
+        double2 *d = reinterpret_cast<double2 *>(recA + c * 8);
         d[0] = make_double2(v[0], v[1]);
         d[1] = make_double2(v[2], v[3]);
         d[2] = make_double2(v[4], v[5]);
         d[3] = make_double2(v[6], 0.0);
       }
       if (arec64) {
-        double2 *d = reinterpret_cast<double2 *>(arec64 + e * 8);
+        double2 *d = reinterpret_cast<double2 *>(arec64 + c * 8);
         d[0] = make_double2(v[0], v[1]);
         d[1] = make_double2(v[2], v[3]);
         d[2] = make_double2(v[4], v[5]);
@@ -166,7 +153,7 @@ cudaError_t launch_pack_records(const PackSrc &S, const DevBlock &hb, double *a7
 }
 
 __global__ void __launch_bounds__(kWalkThreads) k_to_plan(const double *src, double *dst, DevBlock hb) {
-  walk_rows(hb, [&](int, int, int, int p, long long, long long e) { dst[e] = src[p]; });
+  walk_rows(hb, [&](int, int, int, int p, long long c) { dst[c] = src[p]; });
 }
 
 cudaError_t launch_to_plan_f64(const double *src, double *dst, const DevBlock &hb, cudaStream_t st) {
@@ -175,7 +162,7 @@ cudaError_t launch_to_plan_f64(const double *src, double *dst, const DevBlock &h
 }
 
 __global__ void __launch_bounds__(kWalkThreads) k_from_plan(const double *src, double *dst, DevBlock hb) {
-  walk_rows(hb, [&](int, int, int, int p, long long, long long e) { dst[p] = src[e]; });
+  walk_rows(hb, [&](int, int, int, int p, long long c) { dst[p] = src[c]; });
 }
 
 cudaError_t launch_from_plan_f64(const double *src, double *dst, const DevBlock &hb, cudaStream_t st) {
@@ -192,7 +179,7 @@ __global__ void k_export(const TF *recF, const TF *recB, Out7 O, DevBlock hb) {
     const int i = (int)(p % hb.nx);
     const int j = (int)((p / hb.nx) % hb.ny);
     const int k = (int)(p / ((long long)hb.nx * hb.ny));
-    const long long a = tile_elem(hb, i, j, k);
+    const long long a = plan_cell(hb, i, j, k);
     const TF *f = recF + a * 4;
     const TF *b = recB + a * 4;
     O.o[0][p] = (double)f[REC_LB];

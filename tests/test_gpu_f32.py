@@ -36,20 +36,6 @@ def test_per_iteration_parity(shape, kind, sym_null):
     g.close()
 
 
-@pytest.mark.parametrize("tile", [(32, 8, 1, 8), (32, 8, 2, 4), (32, 4, 4, 8), (32, 16, 4, 4), (32, 2, 2, 4),
-                                  (32, 16, 2, 8), (32, 12, 2, 8), (32, 6, 1, 4), (32, 32, 4, 8)])
-def test_fp32_tile_shapes(tile):
-    """(tile_j, tile_k, rows_per_thread, stages) of the FP32 sweeps (1, 2 or 4
-    rows per warp, up to 8 warps, 4 or 8 stages): the iterates of the
-    single-precision mode against the oracle's float solve."""
-    blk = W.make_block(37, 45, 23, seed=85, kind="convdiff")
-    g = GpuSystem(blk, mode=sip.SIP_MODE_F32, tile=tile)
-    g.plan.iterate(3)
-    x, it, rel, hist = _oracle(blk, 3)
-    assert np.abs(g.xs() - x).max() <= 1e-5 * np.abs(x).max()
-    g.close()
-
-
 def test_fp32_coefficients_input():
     blk = W.make_block(33, 35, 18, seed=82, kind="convdiff")
     g = GpuSystem(blk, mode=sip.SIP_MODE_F32, coef_f32=True)
