@@ -71,14 +71,14 @@ def parse(argv=None):
     ap.add_argument("--no-ttol", action="store_true", help="skip the time-to-1e-8 solves")
     ap.add_argument("--no-inner-sweep", action="store_true",
                     help="time-to-1e-8 of the refined form with the default inner count only (skip m = 1, 2, 8)")
-    ap.add_argument("--small-solves", type=int, default=100, help="solves of the 32^3 latency measurement")
+    ap.add_argument("--small-solves", type=int, default=200, help="solves of the 32^3 latency measurement")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving measurement (0: skip)")
     ap.add_argument("--serve-max-n", type=int, default=48, help="largest cube edge of a served request")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-block batched-mesh measurement")
     ap.add_argument("--no-small", action="store_true", help="skip the 32^3 solve-latency measurement")
-    ap.add_argument("--large", action="store_true",
-                    help="also solve the 384^3 Peclet-10 block with FP32 coefficients (alpha 0.5 and 0.92)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 384^3 Peclet-10 block with FP32 coefficients (alpha 0.5 and 0.92)")
     ap.add_argument("--batched-iters", type=int, default=12,
                     help="corrections (refined) / iterations (fp64) timed on the batched mesh")
     return ap.parse_args(argv)
@@ -330,8 +330,9 @@ def run_gb300(args):
     # A stays allocated: the inner-count sweep of the time-to-1e-8 factors more plans from it
 
     def step(plan):
+        # a fixed number of corrections (rtol 0: the stop rule never fires)
         x.zero_()
-        return plan.solve(1e-8, args.iters)
+        return plan.solve(0.0, args.iters)
 
     def timed(plan, inner, K, prof=False):
         barrier()
@@ -453,7 +454,8 @@ def run_gb300(args):
         "warmup": args.warmup, "ms_per_step": round(ms_r / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"poisson_{args.n}cube", "cells": N, "alpha": 0.92, "mode": "f32_refined",
-                   "inner_iters": args.inner, "max_corrections_per_step": args.iters, "rtol": 1e-8,
+                   "inner_iters": args.inner, "corrections_per_step": args.iters,
+                   "stop_rule": "none: a fixed number of corrections per step (rtol 0)",
                    "tile": dict(zip(("rows_per_thread", "tile_k", "stages"), plan_r.shape())),
                    "parallelism": f"replicas x{world}", "l2": "working set > L2 (plan arrays "
                    f"{plan_r.nbytes() / 1e9:.2f} GB)", "step": "sip_solve on the factored plan, x reset to 0"},
@@ -476,7 +478,7 @@ def run_gb300(args):
         line["small"] = small(args, local)
     if not args.no_batched and world == 1:
         line["batched"] = batched(args, local)
-    if args.large and world == 1:
+    if not args.no_large and world == 1:
         line["large"] = large(args, local)
     if args.serve_requests > 0 and world == 1:
         line["serving"] = serving(args, local)
@@ -569,13 +571,21 @@ def large(args, local):
     ms, it, rel, conv = _solve_timed(plan, x, stream, 1e-8, 3000)
     import numpy as np
     xs = x.cpu().numpy()
+    # FP64 relative residual of the returned x under the stored FP32 matrix (widened)
+    rn32, bn = ctx.residual_norm(desc)
     out["f32_refined_alpha05"] = {"seconds": round(ms / 1e3, 3), "corrections": it, "sip_iterations": it * 4,
                                   "relres": rel, "converged": bool(conv),
+                                  "relres_fp64_A32": rn32 / bn,
                                   "err_vs_xstar": float(np.linalg.norm(xs - blk.xstar) / np.linalg.norm(blk.xstar))}
     plan.close()
+    x_ref = x.clone()
     del A
     torch.cuda.empty_cache()
     A = [torch.from_numpy(c).cuda() for c in blk.coef_list()]
+    # ... and under the FP64 matrix the generator drew
+    rn64, bn64 = ctx.residual_norm(sip.make_desc(blk.nx, blk.ny, blk.nz, A, b, x_ref))
+    out["f32_refined_alpha05"]["relres_fp64_A64"] = rn64 / bn64
+    del x_ref
     desc = sip.make_desc(blk.nx, blk.ny, blk.nz, A, b, x)
     plan = sip.Plan(ctx, [desc], sip.default_options(mode=sip.SIP_MODE_F64, alpha=0.5, graphs=1))
     ms, it, rel, conv = _solve_timed(plan, x, stream, 1e-8, 5000)
