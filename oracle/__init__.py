@@ -69,6 +69,8 @@ def lib():
         L.oracle_solve_f32.restype = I
         L.oracle_solve_mb.argtypes = [I, P, P, P, P, P, I, P, I, D, I, P, P]
         L.oracle_solve_mb.restype = I
+        L.oracle_solve_refined_mb.argtypes = [I, P, P, P, P, P, P, I, P, I, D, I, I, P, P]
+        L.oracle_solve_refined_mb.restype = I
         _lib = L
     return _lib
 
@@ -241,6 +243,36 @@ def solve_multiblock(blocks, ifaces, factors, x0=None, rtol=1e-8, max_iters=100,
     rel = ctypes.c_double(0.0)
     it = lib().oracle_solve_mb(nb, _p(dims), Pa, Pf, Pb, Px, len(ifaces), _p(ifc), 1 if symmetric else 0,
                                float(rtol), int(max_iters), _p(hist), ctypes.byref(rel))
+    return X, it, rel.value, hist[: it + 1].copy()
+
+
+def solve_refined_multiblock(blocks, ifaces, coefs32, factors32, x0=None, rtol=1e-8, max_outer=100, m_inner=4,
+                             symmetric=False):
+    """FP64 refinement around m single-precision SIP iterations over blocks
+    coupled across x interfaces, the blocks exchanging their interface values
+    of the correction after every inner iteration.
+
+    blocks: list of (nx, ny, nz, coefs64, b); coefs32: per block the FP32
+    coefficient dict; factors32: per block the 7 FP32 factor arrays.
+    Returns (xs, outer_corrections, relres, hist)."""
+    nb = len(blocks)
+    dims = np.array([[bl[0], bl[1], bl[2]] for bl in blocks], dtype=np.int32).reshape(-1)
+    A = [_coefs(bl[3]) for bl in blocks]
+    A32 = [_coefs(c, _f32) for c in coefs32]
+    F = [[_f32(f) for f in fs] for fs in factors32]
+    B = [_f64(bl[4]) for bl in blocks]
+    X = [np.zeros(bl[0] * bl[1] * bl[2]) if x0 is None else _f64(x0[i]).copy() for i, bl in enumerate(blocks)]
+    Pa = (ctypes.c_void_p * (7 * nb))(*[a.ctypes.data for arrs in A for a in arrs])
+    Pa32 = (ctypes.c_void_p * (7 * nb))(*[a.ctypes.data for arrs in A32 for a in arrs])
+    Pf = (ctypes.c_void_p * (7 * nb))(*[f.ctypes.data for fs in F for f in fs])
+    Pb = (ctypes.c_void_p * nb)(*[b.ctypes.data for b in B])
+    Px = (ctypes.c_void_p * nb)(*[x.ctypes.data for x in X])
+    ifc = np.array([list(q) for q in ifaces], dtype=np.int32).reshape(-1) if ifaces else np.zeros(4, np.int32)
+    hist = np.zeros(max_outer + 1)
+    rel = ctypes.c_double(0.0)
+    it = lib().oracle_solve_refined_mb(nb, _p(dims), Pa, Pa32, Pf, Pb, Px, len(ifaces), _p(ifc),
+                                       1 if symmetric else 0, float(rtol), int(max_outer), int(m_inner),
+                                       _p(hist), ctypes.byref(rel))
     return X, it, rel.value, hist[: it + 1].copy()
 
 

@@ -510,3 +510,138 @@ int oracle_solve_f32(int nx, int ny, int nz,
   if (relres_out) *relres_out = rel;
   return it;
 }
+
+/* ------------------------------------------------------------------ */
+/* The mixed-precision refinement (oracle_solve_refined) over blocks coupled
+ * across x interfaces (oracle_solve_mb's mesh, arguments and lagged
+ * block-Jacobi reading; Sec. 4.1 single-precision solver, Sec. 4.2 exchange
+ * of block-boundary data between iterations).  Reading for the inner
+ * iterations: the correction system is the coupled one, A d = r, and the
+ * blocks exchange their interface values of d after every inner iteration.
+ *
+ * Outer step: the coupled FP64 residual r_b of every block exactly as in
+ * oracle_solve_mb (A: FP64 entries), relres and the stop rule of
+ * oracle_solve; otherwise r32_b = (float) r_b, d_b = 0 and m_inner inner
+ * iterations, each
+ *   c_b = r32_b - sum over the interfaces of b of e32 * d_neighbour
+ *         (float arithmetic, every product and difference rounded to float;
+ *          e32: the interface entry of A32, lo's AE32 / hi's AW32, or lo's
+ *          AE32 for both when sym != 0; d from the previous inner iteration
+ *          of all blocks, so the first inner iteration sees c_b = r32_b),
+ * then for every block one single-precision SIP iteration on A32_b d_b = c_b
+ * from the current d_b (oracle_iterate_f32, from zero in the first), and
+ * finally x_b += (double) d_b.
+ * A: FP64 entries, 7 per block; A32: FP32 entries, 7 per block; F32: FP32
+ * factors lb, lw, ls, lp, un, ue, ut, 7 per block.  Returns the number of
+ * outer corrections; hist (nullable, max_outer + 1) gets relres before each. */
+int oracle_solve_refined_mb(int nb, const int *dims, const double *const *A, const float *const *A32,
+                            const float *const *F32, const double *const *B, double *const *X, int nif,
+                            const int *ifc, int sym, double rtol, int max_outer, int m_inner, double *hist,
+                            double *relres_out) {
+  size_t nmax = 0;
+  for (int b = 0; b < nb; ++b) {
+    size_t n = (size_t)dims[3 * b] * dims[3 * b + 1] * dims[3 * b + 2];
+    if (n > nmax) nmax = n;
+  }
+  double **beff = (double **)malloc(sizeof(double *) * nb);
+  double **r = (double **)malloc(sizeof(double *) * nb);
+  float **r32 = (float **)malloc(sizeof(float *) * nb);
+  float **c32 = (float **)malloc(sizeof(float *) * nb);
+  float **d32 = (float **)malloc(sizeof(float *) * nb);
+  float *w1 = (float *)malloc(nmax * sizeof(float));
+  float *w2 = (float *)malloc(nmax * sizeof(float));
+  float *w3 = (float *)malloc(nmax * sizeof(float));
+  nsum bsum = {0.0, 0.0};
+  for (int b = 0; b < nb; ++b) {
+    size_t n = (size_t)dims[3 * b] * dims[3 * b + 1] * dims[3 * b + 2];
+    beff[b] = (double *)malloc(n * sizeof(double));
+    r[b] = (double *)malloc(n * sizeof(double));
+    r32[b] = (float *)malloc(n * sizeof(float));
+    c32[b] = (float *)malloc(n * sizeof(float));
+    d32[b] = (float *)malloc(n * sizeof(float));
+    nsum_add(&bsum, oracle_dot_sq((int64_t)n, B[b]));
+  }
+  double bb = sqrt(nsum_get(&bsum));
+  double scale = bb > 0.0 ? bb : 1.0;
+  int it = 0;
+  double rel = 0.0;
+  for (;;) {
+    /* coupled FP64 residual of x (as oracle_solve_mb) */
+    for (int b = 0; b < nb; ++b) {
+      size_t n = (size_t)dims[3 * b] * dims[3 * b + 1] * dims[3 * b + 2];
+      memcpy(beff[b], B[b], n * sizeof(double));
+    }
+    for (int q = 0; q < nif; ++q) {
+      int lo = ifc[4 * q], hi = ifc[4 * q + 1], nj = ifc[4 * q + 2], nk = ifc[4 * q + 3];
+      int nxl = dims[3 * lo], nyl = dims[3 * lo + 1];
+      int nxh = dims[3 * hi], nyh = dims[3 * hi + 1];
+      for (int k = 0; k < nk; ++k)
+        for (int j = 0; j < nj; ++j) {
+          size_t pl = (size_t)(nxl - 1) + (size_t)nxl * ((size_t)j + (size_t)nyl * k);
+          size_t ph = (size_t)nxh * ((size_t)j + (size_t)nyh * k);
+          double elo = A[7 * lo + 2][pl];
+          double ehi = sym ? elo : A[7 * hi + 1][ph];
+          beff[lo][pl] -= elo * X[hi][ph];
+          beff[hi][ph] -= ehi * X[lo][pl];
+        }
+    }
+    nsum rs = {0.0, 0.0};
+    for (int b = 0; b < nb; ++b) {
+      int nx = dims[3 * b], ny = dims[3 * b + 1], nz = dims[3 * b + 2];
+      const double *const *a = A + 7 * b;
+      nsum_add(&rs, oracle_residual(nx, ny, nz, a[0], a[1], a[2], a[3], a[4], a[5], a[6], beff[b], X[b], r[b]));
+    }
+    rel = sqrt(nsum_get(&rs)) / scale;
+    if (hist) hist[it] = rel;
+    if (rel <= rtol || it >= max_outer) break;
+    for (int b = 0; b < nb; ++b) {
+      size_t n = (size_t)dims[3 * b] * dims[3 * b + 1] * dims[3 * b + 2];
+      for (size_t p = 0; p < n; ++p) {
+        r32[b][p] = (float)r[b][p];
+        d32[b][p] = 0.0f;
+      }
+    }
+    for (int m = 0; m < m_inner; ++m) {
+      /* exchange: interface terms of the previous inner iteration's d */
+      for (int b = 0; b < nb; ++b) {
+        size_t n = (size_t)dims[3 * b] * dims[3 * b + 1] * dims[3 * b + 2];
+        memcpy(c32[b], r32[b], n * sizeof(float));
+      }
+      for (int q = 0; q < nif; ++q) {
+        int lo = ifc[4 * q], hi = ifc[4 * q + 1], nj = ifc[4 * q + 2], nk = ifc[4 * q + 3];
+        int nxl = dims[3 * lo], nyl = dims[3 * lo + 1];
+        int nxh = dims[3 * hi], nyh = dims[3 * hi + 1];
+        for (int k = 0; k < nk; ++k)
+          for (int j = 0; j < nj; ++j) {
+            size_t pl = (size_t)(nxl - 1) + (size_t)nxl * ((size_t)j + (size_t)nyl * k);
+            size_t ph = (size_t)nxh * ((size_t)j + (size_t)nyh * k);
+            float elo = A32[7 * lo + 2][pl];
+            float ehi = sym ? elo : A32[7 * hi + 1][ph];
+            float tl = elo * d32[hi][ph];
+            float th = ehi * d32[lo][pl];
+            c32[lo][pl] = c32[lo][pl] - tl;
+            c32[hi][ph] = c32[hi][ph] - th;
+          }
+      }
+      /* one single-precision SIP iteration per block */
+      for (int b = 0; b < nb; ++b) {
+        int nx = dims[3 * b], ny = dims[3 * b + 1], nz = dims[3 * b + 2];
+        const float *const *a = A32 + 7 * b;
+        const float *const *f = F32 + 7 * b;
+        oracle_iterate_f32(nx, ny, nz, a[0], a[1], a[2], a[3], a[4], a[5], a[6], f[0], f[1], f[2], f[3], f[4],
+                           f[5], f[6], c32[b], d32[b], m == 0, w1, w2, w3);
+      }
+    }
+    for (int b = 0; b < nb; ++b) {
+      size_t n = (size_t)dims[3 * b] * dims[3 * b + 1] * dims[3 * b + 2];
+      for (size_t p = 0; p < n; ++p) X[b][p] += (double)d32[b][p];
+    }
+    ++it;
+  }
+  for (int b = 0; b < nb; ++b) {
+    free(beff[b]); free(r[b]); free(r32[b]); free(c32[b]); free(d32[b]);
+  }
+  free(beff); free(r); free(r32); free(c32); free(d32); free(w1); free(w2); free(w3);
+  if (relres_out) *relres_out = rel;
+  return it;
+}
