@@ -681,7 +681,7 @@ def batched(args, local):
                                       "sip_iterations": it * inner, "relres": rel, "converged": bool(conv)}}
         plan.close()
     # time to 1e-8 of the refined form with fewer FP32 iterations per correction
-    # (the interface coupling is refreshed once per correction)
+    # (interfaces exchanged after every inner FP32 iteration)
     if not args.no_inner_sweep:
         ifs = [sip.sip_interface(lo, hi, nj, nk) for lo, hi, nj, nk in mesh.ifaces]
         for m in (1, 2):

@@ -92,6 +92,10 @@ typedef struct {
  * the coupling enters each block's residual with the neighbour's values from
  * the previous iteration (lagged, block Jacobi), so relres and the stop rule
  * refer to the coupled system while each block relaxes with its own factors.
+ * In SIP_MODE_F32_REFINED the inner FP32 iterations solve the coupled
+ * correction system: after every inner iteration the blocks exchange the
+ * interface values of their FP32 correction, whose coupling terms (entries
+ * rounded to FP32) enter the next inner residual.
  * Rules: 0 <= blk_lo, blk_hi < nblocks, blk_lo != blk_hi; 1 <= nj <= both
  * blocks' ny, 1 <= nk <= both blocks' nz; each block face carries at most one
  * interface.  Otherwise sip_factor returns SIP_ERR_INVALID_ARG. */

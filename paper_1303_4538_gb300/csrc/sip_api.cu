@@ -157,6 +157,7 @@ struct sip_plan {
   // right-hand side the residual kernels read) before every iteration
   std::vector<sip_interface> ifaces;
   double *beff64 = nullptr;
+  float *hsave32 = nullptr;  // refined mode: interface cells' r32 from the outer residual
   HaloEntry *halo = nullptr;
   int nhalo = 0;
   // captured iterations (sip_options.graphs): graph[0] replays one iteration,
@@ -427,6 +428,10 @@ int enqueue_iter_refined(sip_plan *p) {
     if (first) {
       rc = enqueue_forward(p, K_FWD32, (const float *)p->r32, p->y32);  // d = 0: the residual is r
     } else {
+      // exchange: the interface terms of the neighbours' current correction
+      // (the inner system is the coupled one)
+      if (p->nhalo > 0)
+        UTIL(launch_halo32(p->halo, p->nhalo, p->r32, p->d32, p->hsave32, q == 1, p->ctl, ctx->stream));
       rc = enqueue_resid(p, K_RES32, (const float *)p->recA, (const float *)p->r32, (const float *)p->d32, p->y32,
                          false);
       if (!rc) rc = enqueue_forward(p, K_FWD32, (const float *)p->y32, p->y32);
@@ -1149,6 +1154,7 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     HaloSrc *dsrc = nullptr;
     PA(p->beff64, N);
     PA(p->halo, p->nhalo);
+    PA(p->hsave32, p->nhalo);
     PA(dsrc, hsrcs.size());
     cudaError_t e = cudaMemcpyAsync(p->halo, hents.data(), hents.size() * sizeof(HaloEntry),
                                     cudaMemcpyHostToDevice, st);

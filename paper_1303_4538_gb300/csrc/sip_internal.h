@@ -218,6 +218,10 @@ struct HaloSrc {
 cudaError_t launch_halo_coefs(const HaloSrc *src, int nsrc, HaloEntry *ent, int coef_f32, cudaStream_t st);
 cudaError_t launch_halo(const HaloEntry *ent, int nent, const double *b, const double *x, double *beff,
                         const Ctl *ctl, cudaStream_t st);
+// the refinement's inner exchange: interface cells of r32 minus the coupling
+// terms of the current FP32 correction d (first: save r32's values first)
+cudaError_t launch_halo32(const HaloEntry *ent, int nent, float *r32, const float *d, float *save, bool first,
+                          const Ctl *ctl, cudaStream_t st);
 
 // finalize modes
 constexpr int FIN_BNORM = 0;   // partials are ||b||^2 pieces: set ctl->bnorm

@@ -300,6 +300,38 @@ cudaError_t launch_halo(const HaloEntry *ent, int nent, const double *b, const d
   return cudaGetLastError();
 }
 
+// Interface terms of the refinement's inner correction system (the blocks
+// exchange the correction d after every inner iteration): the FP32
+// right-hand side of an interface cell becomes
+//   r32[cell] = r0 - c0 d[nb0] (- c1 d[nb1]),
+// each product and difference rounded to float in that order (c: the
+// coupling entries rounded to float; r0: the cell's value from the outer
+// FP64 residual, saved by the first call of a correction and restored from
+// the copy afterwards).  Skipped once the stop rule has fired.
+__global__ void k_halo32(const HaloEntry *ent, int nent, float *r32, const float *d, float *save, int first,
+                         const Ctl *ctl) {
+  if (ctl->done) return;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nent; q += gridDim.x * blockDim.x) {
+    const HaloEntry e = ent[q];
+    float r0;
+    if (first) {
+      r0 = r32[e.cell];
+      save[q] = r0;
+    } else {
+      r0 = save[q];
+    }
+    float v = __fsub_rn(r0, __fmul_rn((float)e.c[0], d[e.nb[0]]));
+    if (e.nb[1] >= 0) v = __fsub_rn(v, __fmul_rn((float)e.c[1], d[e.nb[1]]));
+    r32[e.cell] = v;
+  }
+}
+
+cudaError_t launch_halo32(const HaloEntry *ent, int nent, float *r32, const float *d, float *save, bool first,
+                          const Ctl *ctl, cudaStream_t st) {
+  k_halo32<<<util_grid(nent), 256, 0, st>>>(ent, nent, r32, d, save, first ? 1 : 0, ctl);
+  return cudaGetLastError();
+}
+
 __global__ void k_cast_f64_f32(const double *src, float *dst, long long n) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
     dst[q] = (float)src[q];

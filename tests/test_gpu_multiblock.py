@@ -69,6 +69,37 @@ def test_refined_solve_reaches_tolerance(dims, kind):
     g.close()
 
 
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("dims,kind", MESHES)
+def test_refined_per_correction_parity(dims, kind):
+    """FP64 refinement around m FP32 iterations on the coupled correction
+    system (interface exchange after every inner iteration) against the
+    oracle's float arithmetic, per correction (C13: rel 1e-5)."""
+    mesh = W.make_mesh(dims, 29, kind)
+    sym = mesh.blocks[0].symmetric
+    F32 = [oracle.factors_f32(oracle.factor(b.nx, b.ny, b.nz, b.coefs, 0.92)) for b in mesh.blocks]
+    c32 = [{k: v.astype(np.float32) for k, v in b.coefs.items()} for b in mesh.blocks]
+    blocks = [(b.nx, b.ny, b.nz, b.coefs, b.b) for b in mesh.blocks]
+    for m in (1, 2, 4):
+        g = GpuSystem(mesh.blocks, ifaces=mesh.ifaces, mode=sip.SIP_MODE_F32_REFINED, inner=m, sym_null=sym)
+        for n in (1, 3):
+            for x in g.x:
+                x.zero_()
+            g.plan.iterate(n)
+            xs, it, rel, hist = oracle.solve_refined_multiblock(blocks, mesh.ifaces, c32, F32, rtol=-1.0,
+                                                                max_outer=n, m_inner=m, symmetric=sym)
+            hg = np.array(g.plan.history())
+            assert len(hg) == n
+            assert abs(hg[0] - hist[0]) <= 1e-12
+            assert np.abs(hg - hist[:n]).max() <= 1e-5 * hist[0]
+            for q, x in enumerate(xs):
+                assert _rel(g.xs(q), x) <= 1e-5
+        g.close()
+
+
 def test_interface_validation():
     blocks = [W.make_block(4, 3, 3, seed=1), W.make_block(3, 4, 2, seed=2)]
     for bad in ([(0, 0, 3, 2)], [(0, 2, 3, 2)], [(0, 1, 4, 2)], [(0, 1, 3, 3)], [(0, 1, 3, 2), (0, 1, 2, 2)],
