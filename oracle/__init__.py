@@ -71,6 +71,8 @@ def lib():
         L.oracle_solve_mb.restype = I
         L.oracle_solve_refined_mb.argtypes = [I, P, P, P, P, P, P, I, P, I, D, I, I, P, P]
         L.oracle_solve_refined_mb.restype = I
+        L.oracle_assemble_pcorr.argtypes = [I, I, I] + [P] * 8 + [I] + [P] * 8
+        L.oracle_assemble_pcorr.restype = None
         _lib = L
     return _lib
 
@@ -274,6 +276,22 @@ def solve_refined_multiblock(blocks, ifaces, coefs32, factors32, x0=None, rtol=1
                                        1 if symmetric else 0, float(rtol), int(max_outer), int(m_inner),
                                        _p(hist), ctypes.byref(rel))
     return X, it, rel.value, hist[: it + 1].copy()
+
+
+def assemble_pcorr(nx, ny, nz, dx, dy, dz, rho, g, ux, uy, uz, dirichlet_bottom=True):
+    """Pressure-correction coefficients and right-hand side of one block on a
+    rectilinear grid (the routine celp2 of Sec. 3.1).  Returns (coefs, b):
+    coefs a dict ap, aw, ae, as, an, ab, at of natural-layout FP64 arrays."""
+    n = nx * ny * nz
+    ins = [_f64(v) for v in (dx, dy, dz, rho, g, ux, uy, uz)]
+    assert ins[0].size == nx and ins[1].size == ny and ins[2].size == nz
+    assert ins[3].size == n and ins[4].size == n
+    assert ins[5].size == (nx + 1) * ny * nz and ins[6].size == nx * (ny + 1) * nz
+    assert ins[7].size == nx * ny * (nz + 1)
+    out = [np.zeros(n) for _ in range(8)]
+    lib().oracle_assemble_pcorr(nx, ny, nz, *[_p(v) for v in ins], 1 if dirichlet_bottom else 0,
+                                *[_p(v) for v in out])
+    return dict(zip(COEF_NAMES, out[:7])), out[7]
 
 
 def norm2(v) -> float:

@@ -645,3 +645,82 @@ int oracle_solve_refined_mb(int nb, const int *dims, const double *const *A, con
   if (relres_out) *relres_out = rel;
   return it;
 }
+
+/* ------------------------------------------------------------------ */
+/* Pressure-correction coefficient assembly (the routine celp2 of Sec. 3.1,
+ * Table 1, whose symmetric system Sec. 4.1 solves; the paper does not print
+ * its discretisation).  Reading (an invented, stated FV geometry): a block of
+ * nx x ny x nz hexahedral cells on a rectilinear grid with cell widths
+ * dx[i], dy[j], dz[k]; per cell a density rho and the momentum equation's
+ * V / a_P ("g"); face-normal velocities u* on every face (ux: (nx+1) ny nz
+ * faces, face i the west face of cell i, index (k ny + j)(nx+1) + i; uy:
+ * nx (ny+1) nz, index (k (ny+1) + j) nx + i; uz: nx ny (nz+1), index
+ * (k ny + j) nx + i).  The SIMPLE-type pressure-correction equation
+ * -div(rho g grad p') = -div(rho u*) in finite volumes:
+ *   interior face f between P and N:
+ *     rho_f = (rho_P + rho_N) * 0.5,  g_f = (g_P + g_N) * 0.5,
+ *     delta_f = (w_P + w_N) * 0.5  (w: the cells' widths along the face normal),
+ *     S_f = the face area (dy dz, dx dz or dx dy of P),
+ *     A_N(P) = -(((rho_f * g_f) * S_f) / delta_f);
+ *   boundary faces are walls (coefficient 0), except the k = 0 face when
+ *   dirichlet_bottom != 0 (p' = 0 beyond it): it adds
+ *     cB = ((rho_P * g_P) * S_z) / (dz[0] * 0.5) to AP;
+ *   AP = ((((((-AW) + (-AE)) + (-AS)) + (-AN)) + (-AB)) + (-AT)) + cB;
+ *   mass fluxes F_f = (rho_f * u*_f) * S_f (boundary faces: rho_f = rho_P),
+ *   b = -(((((F_e - F_w) + F_n) - F_s) + F_t) - F_b), the negative net outflow.
+ * All in double, in exactly that order. */
+void oracle_assemble_pcorr(int nx, int ny, int nz, const double *dx, const double *dy, const double *dz,
+                           const double *rho, const double *g, const double *ux, const double *uy,
+                           const double *uz, int dirichlet_bottom, double *ap, double *aw, double *ae,
+                           double *as, double *an, double *ab, double *at, double *b) {
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t p = (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * k);
+        double Sx = dy[j] * dz[k], Sy = dx[i] * dz[k], Sz = dx[i] * dy[j];
+        /* neighbour cell indices and widths along each axis */
+        double c[6] = {0, 0, 0, 0, 0, 0}; /* W E S N B T coefficients */
+        double rf[6];                      /* face densities for the fluxes */
+        int has[6] = {i > 0, i < nx - 1, j > 0, j < ny - 1, k > 0, k < nz - 1};
+        size_t nb[6] = {p - 1, p + 1, p - (size_t)nx, p + (size_t)nx, p - (size_t)nx * ny, p + (size_t)nx * ny};
+        double w[6], S[6] = {Sx, Sx, Sy, Sy, Sz, Sz};
+        w[0] = has[0] ? dx[i - 1] : 0.0;
+        w[1] = has[1] ? dx[i + 1] : 0.0;
+        w[2] = has[2] ? dy[j - 1] : 0.0;
+        w[3] = has[3] ? dy[j + 1] : 0.0;
+        w[4] = has[4] ? dz[k - 1] : 0.0;
+        w[5] = has[5] ? dz[k + 1] : 0.0;
+        double wp[6] = {dx[i], dx[i], dy[j], dy[j], dz[k], dz[k]};
+        for (int f = 0; f < 6; ++f) {
+          if (has[f]) {
+            double rhof = (rho[p] + rho[nb[f]]) * 0.5;
+            double gf = (g[p] + g[nb[f]]) * 0.5;
+            double delta = (wp[f] + w[f]) * 0.5;
+            c[f] = -(((rhof * gf) * S[f]) / delta);
+            rf[f] = rhof;
+          } else {
+            rf[f] = rho[p];
+          }
+        }
+        double cB = 0.0;
+        if (k == 0 && dirichlet_bottom) cB = ((rho[p] * g[p]) * Sz) / (dz[0] * 0.5);
+        aw[p] = c[0];
+        ae[p] = c[1];
+        as[p] = c[2];
+        an[p] = c[3];
+        ab[p] = c[4];
+        at[p] = c[5];
+        ap[p] = ((((((-c[0]) + (-c[1])) + (-c[2])) + (-c[3])) + (-c[4])) + (-c[5])) + cB;
+        /* face velocities: west / east (x), south / north (y), bottom / top (z) */
+        double uw = ux[((size_t)k * ny + j) * (size_t)(nx + 1) + i];
+        double ue = ux[((size_t)k * ny + j) * (size_t)(nx + 1) + i + 1];
+        double us = uy[((size_t)k * (ny + 1) + j) * (size_t)nx + i];
+        double un = uy[((size_t)k * (ny + 1) + j + 1) * (size_t)nx + i];
+        double ub = uz[((size_t)k * ny + j) * (size_t)nx + i];
+        double ut = uz[((size_t)(k + 1) * ny + j) * (size_t)nx + i];
+        double Fw = (rf[0] * uw) * Sx, Fe = (rf[1] * ue) * Sx;
+        double Fs = (rf[2] * us) * Sy, Fn = (rf[3] * un) * Sy;
+        double Fb = (rf[4] * ub) * Sz, Ft = (rf[5] * ut) * Sz;
+        b[p] = -(((((Fe - Fw) + Fn) - Fs) + Ft) - Fb);
+      }
+}

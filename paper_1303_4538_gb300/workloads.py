@@ -234,3 +234,59 @@ def batched_mesh(seed: int = 4541) -> Mesh:
     """The 64-block convection-diffusion mesh of ~20 M cells (x chain)."""
     dims, _ = batched_mesh_dims(seed)
     return make_mesh(dims, seed, kind="convdiff")
+
+
+@dataclass
+class PcorrInputs:
+    """Inputs of the pressure-correction assembly on one rectilinear block:
+    cell widths dx (nx), dy (ny), dz (nz); per cell the density ``rho`` and the
+    momentum equation's V / a_P (``g``); face-normal velocities u* on every
+    face: ``ux`` ((nx+1) ny nz, face i = west face of cell i, index
+    (k ny + j)(nx+1) + i), ``uy`` (nx (ny+1) nz, index (k (ny+1) + j) nx + i),
+    ``uz`` (nx ny (nz+1), index (k ny + j) nx + i)."""
+
+    nx: int
+    ny: int
+    nz: int
+    dx: np.ndarray
+    dy: np.ndarray
+    dz: np.ndarray
+    rho: np.ndarray
+    g: np.ndarray
+    ux: np.ndarray
+    uy: np.ndarray
+    uz: np.ndarray
+    dirichlet_bottom: bool = True
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+def pcorr_inputs(nx: int, ny: int, nz: int, seed: int, dirichlet_bottom: bool = True) -> PcorrInputs:
+    """Seeded inputs of the pressure-correction assembly: a stretched grid
+    (widths U[0.5, 2] / n per axis), rho ~ U[0.8, 1.2], g ~ U[0.5, 2],
+    interior-face velocities u* ~ N(0, 1), zero velocity on the wall faces
+    (x and y boundaries, top), u* ~ N(0, 1) on the bottom (Dirichlet, open)
+    face.  Draw order: dx, dy, dz, rho, g, ux, uy, uz."""
+    if min(nx, ny, nz) < 1:
+        raise ValueError("block dimensions must be >= 1")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dx = rng.uniform(0.5, 2.0, size=nx) / nx
+    dy = rng.uniform(0.5, 2.0, size=ny) / ny
+    dz = rng.uniform(0.5, 2.0, size=nz) / nz
+    n = nx * ny * nz
+    rho = rng.uniform(0.8, 1.2, size=n)
+    g = rng.uniform(0.5, 2.0, size=n)
+    ux = rng.standard_normal(size=(nz, ny, nx + 1))
+    uy = rng.standard_normal(size=(nz, ny + 1, nx))
+    uz = rng.standard_normal(size=(nz + 1, ny, nx))
+    ux[:, :, 0] = 0.0
+    ux[:, :, nx] = 0.0
+    uy[:, 0, :] = 0.0
+    uy[:, ny, :] = 0.0
+    uz[nz, :, :] = 0.0
+    if not dirichlet_bottom:
+        uz[0, :, :] = 0.0
+    return PcorrInputs(nx, ny, nz, dx, dy, dz, rho, g, ux.reshape(-1).copy(), uy.reshape(-1).copy(),
+                       uz.reshape(-1).copy(), dirichlet_bottom)
