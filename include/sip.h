@@ -230,6 +230,45 @@ int sip_residual_norm(sip_ctx *ctx, const sip_block_desc *blk, double *rnorm_out
 #define SIP_NOALLOC_MAX_CELLS 67108864LL
 int sip_residual_norm_noalloc(sip_ctx *ctx, const sip_block_desc *blk, double *norms_dev);
 
+/* ---- Pressure-correction coefficient assembly ---------------------------
+ * The routine celp2 of Sec. 3.1 (Table 1) builds the symmetric
+ * pressure-correction system (Sec. 4.1) that SIP then solves; the paper does
+ * not print its discretisation.  This library's stated geometry: one block of
+ * nx x ny x nz hexahedral cells on a rectilinear grid, natural layout
+ * p = i + nx (j + ny k).  Inputs (device memory of the context's device, FP64):
+ *   dx[nx], dy[ny], dz[nz]   cell widths;
+ *   rho[n], g[n]             per cell: density and the momentum equation's V / a_P;
+ *   ux[(nx+1) ny nz]         x-face normal velocities u*, face i = the west face
+ *                            of cell i, index (k ny + j)(nx+1) + i;
+ *   uy[nx (ny+1) nz]         y faces, face j = the south face of cell j,
+ *                            index (k (ny+1) + j) nx + i;
+ *   uz[nx ny (nz+1)]         z faces, face k = the bottom face of cell k,
+ *                            index (k ny + j) nx + i;
+ *   dirichlet_bottom         1: p' = 0 beyond the k = 0 face (else a wall).
+ * Outputs (device, n doubles each): the seven coefficient arrays of
+ * sip_block_desc and b, for -div(rho g grad p') = -div(rho u*):
+ *   A_N(P) = -rho_f g_f S_f / delta_f on interior faces (rho_f, g_f the mean
+ *   of the two cells' values, delta_f the mean of their widths along the
+ *   normal, S_f the face area); walls carry no entry; the Dirichlet face adds
+ *   rho_P g_P S_z / (dz_0 / 2) to AP; AP = -(sum of the six entries) + that
+ *   term; b = -(net outflow of rho u* S) with the cell's own rho on boundary
+ *   faces.  Every operation is rounded in a fixed order (no fused
+ *   multiply-adds): the matrix is exactly symmetric.  aw, as, ab may be NULL
+ *   (symmetric storage, sip_block_desc.symmetric = 1: they are not written).
+ * The outputs can be passed to sip_factor directly (no host round trip).
+ * Enqueued on the context's stream, asynchronous; allocates nothing.  Outputs
+ * must not overlap the inputs.  Errors: SIP_ERR_INVALID_ARG (dimensions < 1,
+ * more than 2^31 - 1 cells, a required pointer NULL), SIP_ERR_CUDA. */
+typedef struct {
+  int32_t nx, ny, nz;
+  int32_t dirichlet_bottom;
+  const double *dx, *dy, *dz;
+  const double *rho, *g;
+  const double *ux, *uy, *uz;
+} sip_pcorr_desc;
+int sip_assemble_pcorr(sip_ctx *ctx, const sip_pcorr_desc *in, double *ap, double *aw, double *ae, double *as,
+                       double *an, double *ab, double *at, double *b);
+
 /* ---- Serving (continuous batching of solve requests) ------------------
  * A server runs `max_slots` solver slots, each with its own CUDA stream on the
  * calling thread's current device.  Submitted requests queue in arrival order;

@@ -1374,6 +1374,49 @@ static std::string natblock_from_desc(const sip_block_desc *d, NatBlock *nb) {
   return "";
 }
 
+int sip_assemble_pcorr(sip_ctx *ctx, const sip_pcorr_desc *in, double *ap, double *aw, double *ae, double *as,
+                       double *an, double *ab, double *at, double *b) {
+  if (!ctx) return SIP_ERR_INVALID_ARG;
+  if (!in) return fail(ctx, SIP_ERR_INVALID_ARG, "null descriptor");
+  if (in->nx < 1 || in->ny < 1 || in->nz < 1) return fail(ctx, SIP_ERR_INVALID_ARG, "block dimensions must be >= 1");
+  // the largest face array ((nx + 1) ny nz and the like) indexes with 64-bit integers;
+  // a block must fit the 2^31 - 1 cells of the solver's descriptors
+  if ((long long)in->nx * in->ny * in->nz > 2147483647LL)
+    return fail(ctx, SIP_ERR_INVALID_ARG, "block larger than 2^31 - 1 cells");
+  if (!in->dx || !in->dy || !in->dz || !in->rho || !in->g || !in->ux || !in->uy || !in->uz)
+    return fail(ctx, SIP_ERR_INVALID_ARG, "null input array");
+  if (!ap || !ae || !an || !at || !b) return fail(ctx, SIP_ERR_INVALID_ARG, "null output array");
+  CU(cudaSetDevice(ctx->device));
+  PcorrArgs a;
+  a.nx = in->nx;
+  a.ny = in->ny;
+  a.nz = in->nz;
+  a.dirichlet_bottom = in->dirichlet_bottom ? 1 : 0;
+  a.dx = in->dx;
+  a.dy = in->dy;
+  a.dz = in->dz;
+  a.rho = in->rho;
+  a.g = in->g;
+  a.ux = in->ux;
+  a.uy = in->uy;
+  a.uz = in->uz;
+  a.ap = ap;
+  a.aw = aw;
+  a.ae = ae;
+  a.as = as;
+  a.an = an;
+  a.ab = ab;
+  a.at = at;
+  a.b = b;
+  const long long n = (long long)in->nx * in->ny * in->nz;
+  int sms = 0;
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  // enough CTAs of 256 threads to fill every SM (8 resident each), fewer for small blocks
+  const int grid = (int)std::min<long long>((n + 255) / 256, (long long)sms * 8);
+  CU(launch_assemble_pcorr(a, grid, ctx->stream));
+  return SIP_OK;
+}
+
 int sip_residual_norm(sip_ctx *ctx, const sip_block_desc *blk, double *rnorm_out, double *bnorm_out) {
   if (!ctx) return SIP_ERR_INVALID_ARG;
   NatBlock nb;

@@ -223,6 +223,15 @@ cudaError_t launch_halo(const HaloEntry *ent, int nent, const double *b, const d
 cudaError_t launch_halo32(const HaloEntry *ent, int nent, float *r32, const float *d, float *save, bool first,
                           const Ctl *ctl, cudaStream_t st);
 
+// pressure-correction assembly (sip_assemble.cu): inputs and outputs of one
+// block, device pointers; aw / as / ab may be null (symmetric storage)
+struct PcorrArgs {
+  int nx, ny, nz, dirichlet_bottom;
+  const double *dx, *dy, *dz, *rho, *g, *ux, *uy, *uz;
+  double *ap, *aw, *ae, *as, *an, *ab, *at, *b;
+};
+cudaError_t launch_assemble_pcorr(const PcorrArgs &a, int grid, cudaStream_t st);
+
 // finalize modes
 constexpr int FIN_BNORM = 0;   // partials are ||b||^2 pieces: set ctl->bnorm
 constexpr int FIN_RELRES = 1;  // partials are ||r||^2 pieces: relres, stop rule, counters

@@ -44,7 +44,7 @@ EXPORTED = (
     "sip_plan_destroy", "sip_plane_layout", "sip_profile_enable", "sip_profile_read",
     "sip_launch_count", "sip_kernel_name", "sip_residual_norm",
     "sip_residual_norm_noalloc", "sip_server_start", "sip_server_submit", "sip_server_poll", "sip_server_stop",
-    "sip_server_get_stats",
+    "sip_server_get_stats", "sip_assemble_pcorr",
 )
 
 
@@ -80,6 +80,16 @@ class sip_options(ctypes.Structure):
         ("max_spin", ctypes.c_int64), ("tile_j", ctypes.c_int32), ("tile_k", ctypes.c_int32),
         ("stages", ctypes.c_int32), ("debug_stall", ctypes.c_int32), ("graphs", ctypes.c_int32),
         ("rows_per_thread", ctypes.c_int32), ("autotune", ctypes.c_int32),
+    ]
+
+
+class sip_pcorr_desc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("dirichlet_bottom", ctypes.c_int32),
+        ("dx", ctypes.c_void_p), ("dy", ctypes.c_void_p), ("dz", ctypes.c_void_p),
+        ("rho", ctypes.c_void_p), ("g", ctypes.c_void_p),
+        ("ux", ctypes.c_void_p), ("uy", ctypes.c_void_p), ("uz", ctypes.c_void_p),
     ]
 
 
@@ -132,6 +142,7 @@ def lib():
                                       ctypes.POINTER(D)]
         L.sip_server_stop.argtypes = [P]
         L.sip_server_get_stats.argtypes = [P, ctypes.c_void_p]
+        L.sip_assemble_pcorr.argtypes = [P, ctypes.POINTER(sip_pcorr_desc)] + [P] * 8
         L.sip_kernel_name.restype = ctypes.c_char_p
         for name in EXPORTED:
             if name not in ("sip_default_options", "sip_last_error", "sip_kernel_name"):
@@ -187,6 +198,31 @@ class Context:
                     and out.device.index == self.device):
                 raise ValueError("out must be a float64 tensor of >= 2 elements on the context's device")
         self.check(lib().sip_residual_norm_noalloc(self.h, ctypes.byref(desc), ctypes.c_void_p(_ptr(out))))
+
+    def assemble_pcorr(self, nx: int, ny: int, nz: int, dx, dy, dz, rho, g, ux, uy, uz, outs,
+                       dirichlet_bottom: bool = True) -> None:
+        """sip_assemble_pcorr: pressure-correction coefficients and rhs of one
+        block into `outs` = (ap, aw, ae, as, an, ab, at, b) (device float64
+        tensors of nx*ny*nz; aw / as / ab may be None), in stream order."""
+        import torch
+        n = nx * ny * nz
+        sizes = (nx, ny, nz, n, n, (nx + 1) * ny * nz, nx * (ny + 1) * nz, nx * ny * (nz + 1))
+        for t, m in zip((dx, dy, dz, rho, g, ux, uy, uz), sizes):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == m
+                    and t.device.index == self.device):
+                raise ValueError("inputs must be contiguous float64 tensors of the documented sizes on the "
+                                 "context's device")
+        if len(outs) != 8:
+            raise ValueError("outs: (ap, aw, ae, as, an, ab, at, b)")
+        for q, t in enumerate(outs):
+            if t is None and q in (1, 3, 5):
+                continue
+            if t is None or not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == n
+                                 and t.device.index == self.device):
+                raise ValueError("outputs must be contiguous float64 tensors of nx*ny*nz on the context's device")
+        d = sip_pcorr_desc(nx, ny, nz, 1 if dirichlet_bottom else 0,
+                           *[_ptr(t) for t in (dx, dy, dz, rho, g, ux, uy, uz)])
+        self.check(lib().sip_assemble_pcorr(self.h, ctypes.byref(d), *[ctypes.c_void_p(_ptr(t)) for t in outs]))
 
     def trim(self) -> None:
         """sip_trim: return the pool's cached device memory (not held by a

@@ -46,6 +46,8 @@ int main(void) {
   printf("%zu\n", sizeof(sip_interface));
   printf("%zu %zu %zu %zu\n", sizeof(sip_server_stats), offsetof(sip_server_stats, queued),
          offsetof(sip_server_stats, budget_bytes), offsetof(sip_server_stats, oldest_running_ms));
+  printf("%zu %zu %zu %zu\n", sizeof(sip_pcorr_desc), offsetof(sip_pcorr_desc, dx), offsetof(sip_pcorr_desc, g),
+         offsetof(sip_pcorr_desc, uz));
   return 0;
 }
 ''')
@@ -59,6 +61,8 @@ int main(void) {
             O.rows_per_thread.offset, O.autotune.offset, ctypes.sizeof(I)]
     S = sip.sip_server_stats
     want += [ctypes.sizeof(S), S.queued.offset, S.budget_bytes.offset, S.oldest_running_ms.offset]
+    C = sip.sip_pcorr_desc
+    want += [ctypes.sizeof(C), C.dx.offset, C.g.offset, C.uz.offset]
     assert got == want
 
 
