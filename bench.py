@@ -72,9 +72,12 @@ def parse(argv=None):
     ap.add_argument("--no-inner-sweep", action="store_true",
                     help="time-to-1e-8 of the refined form with the default inner count only (skip m = 1, 2, 8)")
     ap.add_argument("--small-solves", type=int, default=200, help="solves of the 32^3 latency measurement")
-    ap.add_argument("--serve-requests", type=int, default=48, help="requests of the serving measurement (0: skip)")
-    ap.add_argument("--serve-max-n", type=int, default=48, help="largest cube edge of a served request")
-    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-requests", type=int, default=2000, help="requests of the serving measurement (0: skip)")
+    ap.add_argument("--serve-min-n", type=int, default=16, help="smallest cube edge of a served request")
+    ap.add_argument("--serve-max-n", type=int, default=192, help="largest cube edge of a served request")
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-sat", type=int, default=500,
+                    help="requests of the saturation run (a prefix of the request list)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-block batched-mesh measurement")
     ap.add_argument("--no-small", action="store_true", help="skip the 32^3 solve-latency measurement")
     ap.add_argument("--no-assembly", action="store_true", help="skip the pressure-correction assembly measurement")
@@ -763,11 +766,25 @@ def assembly(args, local):
 
 
 def serving(args, local):
-    """Continuous batching of solve requests: Poisson arrivals at 0.8 x the
-    measured serial plain-FP64 capacity; the server (FP32-refined mode, CUDA
-    graphs, `serve_slots` concurrent slots) against a serial plain-FP64 queue
-    replayed with the measured service times.  Latency = arrival -> the host
-    sees the request done."""
+    """The serving workload: ``--serve-requests`` solve requests, cube edge n
+    uniform in [serve_min_n, serve_max_n], Poisson / convection-diffusion
+    generator 50/50, rtol 1e-6 / 1e-8 50/50 (seeded list).  Each request's
+    system is drawn on the device when it arrives (workloads.make_block_device:
+    the make_block recipe with torch's generator), so the host never holds the
+    request stream.  Three measurements:
+      1. serial plain FP64 (plan + solve + release, one request at a time):
+         service times measured on a stratified sample (7 edges spanning the
+         range x 2 generators x 2 tolerances) and interpolated linearly in n
+         within each generator / tolerance class for every request;
+      2. saturation: the first ``serve_sat`` requests offered with a standing
+         backlog (2 x slots queued), sustained solves/s of the server;
+      3. Poisson arrivals at 0.8 x the measured saturation rate over all
+         requests: per-request latency (arrival -> result seen by the host),
+         p50 / p99, solves/s.  The serial FP64 queue is replayed (FIFO, the
+         interpolated service times) on the same arrivals and at 0.8 x its own
+         capacity.
+    Server: FP32-refined mode, CUDA graphs, ``serve_slots`` slots, admitted
+    by HBM footprint."""
     import numpy as np
     import torch
 
@@ -776,83 +793,122 @@ def serving(args, local):
 
     rng = np.random.Generator(np.random.PCG64(4543))
     N = args.serve_requests
-    reqs = []
-    for q in range(N):
-        n = int(rng.integers(16, args.serve_max_n + 1))
-        kind = "poisson" if rng.random() < 0.5 else "convdiff"
-        rtol = 1e-6 if rng.random() < 0.5 else 1e-8
-        blk = W.make_block(n, n, n, seed=4543 * 1000 + q, kind=kind)
-        A = [torch.from_numpy(c).cuda() for c in blk.coef_list()]
-        b = torch.from_numpy(blk.b).cuda()
-        x = torch.zeros(blk.n, dtype=torch.float64, device="cuda")
-        coefs = list(A)
-        if blk.symmetric:
+    lo, hi = args.serve_min_n, args.serve_max_n
+    reqs = [(int(rng.integers(lo, hi + 1)), "poisson" if rng.random() < 0.5 else "convdiff",
+             1e-6 if rng.random() < 0.5 else 1e-8) for _ in range(N)]
+    gs = torch.cuda.Stream()
+    ctx = sip.Context(local, gs.cuda_stream)
+
+    def draw(n, kind, seed):
+        with torch.cuda.stream(gs):
+            c, b, _ = W.make_block_device(n, n, n, seed, kind)
+            x = torch.zeros(n ** 3, dtype=torch.float64, device="cuda")
+        gs.synchronize()
+        coefs = list(c)
+        if kind == "poisson":
             coefs[1] = coefs[3] = coefs[5] = None
-        desc = sip.make_desc(blk.nx, blk.ny, blk.nz, coefs, b, x, symmetric=blk.symmetric)
-        reqs.append(dict(n=n, kind=kind, rtol=rtol, desc=desc, x=x, keep=(A, b, x)))
-    torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
-    ctx = sip.Context(local, stream.cuda_stream)
+        return sip.make_desc(n, n, n, coefs, b, x, symmetric=(kind == "poisson")), (c, b, x)
+
+    # 1. serial plain FP64 on a stratified sample
     o64 = sip.default_options(mode=sip.SIP_MODE_F64)
-    # serial plain FP64: service time of every request (plan + solve + result back)
-    for r in reqs[:2]:
-        r["x"].zero_()
-        p = sip.Plan(ctx, [r["desc"]], o64)
-        p.solve(r["rtol"], 5000)
-        p.close()
-    serv = []
-    for r in reqs:
-        r["x"].zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        p = sip.Plan(ctx, [r["desc"]], o64)
-        p.solve(r["rtol"], 5000)
-        p.close()
-        serv.append(time.perf_counter() - t0)
-    cap = N / sum(serv)
-    lam = 0.8 * cap
-    arr = np.cumsum(rng.exponential(1.0 / lam, size=N))
-    # serial FIFO with the same arrivals
-    end, lat_ser = 0.0, []
-    for a, s_ in zip(arr, serv):
-        end = max(a, end) + s_
-        lat_ser.append(end - a)
-    # served run
-    for r in reqs:
-        r["x"].zero_()
-    torch.cuda.synchronize()
+    edges = sorted(set(int(round(v)) for v in np.linspace(lo, hi, 7)))
+    d, keep = draw(lo, "convdiff", 1)
+    p = sip.Plan(ctx, [d], o64)
+    p.solve(1e-6, 5000)   # warm-up (module load, pool)
+    p.close()
+    svc = {}
+    for kind in ("poisson", "convdiff"):
+        for rtol in (1e-6, 1e-8):
+            ts = []
+            for n in edges:
+                d, keep = draw(n, kind, 7 * n + (kind == "poisson"))
+                gs.synchronize()
+                t0 = time.perf_counter()
+                p = sip.Plan(ctx, [d], o64)
+                p.solve(rtol, 50000)
+                p.close()
+                gs.synchronize()
+                ts.append(time.perf_counter() - t0)
+                del keep
+            svc[(kind, rtol)] = ts
+    serv = np.array([float(np.interp(n, edges, svc[(kind, rtol)])) for n, kind, rtol in reqs])
+    cap_ser = 1.0 / float(serv.mean())
+
     oref = sip.default_options(mode=sip.SIP_MODE_F32_REFINED, graphs=1)
-    srv = sip.Server(ctx, 64 << 30, args.serve_slots)
-    lat, fin, bad = [0.0] * N, [0.0] * N, 0
-    pending = {}
-    t0 = time.perf_counter()
-    i = 0
-    while i < N or pending:
-        now = time.perf_counter() - t0
-        while i < N and arr[i] <= now:
-            pending[srv.submit(reqs[i]["desc"], oref, reqs[i]["rtol"], 5000, keep=reqs[i]["keep"])] = i
-            i += 1
-        for t in list(pending):
-            res = srv.poll(t)
-            if res is not None:
-                k = pending.pop(t)
-                fin[k] = time.perf_counter() - t0
-                lat[k] = fin[k] - arr[k]
-                bad += res[0] != sip.SIP_OK
-        time.sleep(0.0002)
-    sst = srv.stats()
-    srv.stop()
+    slots = args.serve_slots
+
+    def run(count, arrivals):
+        """Serve requests 0..count-1; arrivals None: a standing backlog of
+        2 x slots; else arrival times (s).  Returns (latencies, finish times, t0, failed, stats)."""
+        srv = sip.Server(ctx, 200 << 30, slots)
+        lat, fin = np.zeros(count), np.zeros(count)
+        pending, bad = {}, 0
+        i = done = 0
+        t0 = time.perf_counter()
+        arr = np.zeros(count) if arrivals is None else arrivals
+        while done < count:
+            now = time.perf_counter() - t0
+            while i < count and ((arrivals is None and len(pending) < 2 * slots) or
+                                 (arrivals is not None and arr[i] <= now)):
+                n, kind, rtol = reqs[i]
+                d, keep = draw(n, kind, 4543 * 1000 + i)
+                if arrivals is None:
+                    arr[i] = time.perf_counter() - t0
+                pending[srv.submit(d, oref, rtol, 50000, keep=keep)] = i
+                i += 1
+                now = time.perf_counter() - t0
+            for t in list(pending):
+                res = srv.poll(t)
+                if res is not None:
+                    k = pending.pop(t)
+                    fin[k] = time.perf_counter() - t0
+                    lat[k] = fin[k] - arr[k]
+                    bad += res[0] != sip.SIP_OK
+                    done += 1
+            time.sleep(0.0002)
+        st = srv.stats()
+        srv.stop()
+        return lat, fin, arr, bad, st
+
+    # 2. saturation on a prefix
+    nsat = min(args.serve_sat, N)
+    lat_s, fin_s, arr_s, bad_s, st_s = run(nsat, None)
+    mu = nsat / float(fin_s.max())
+    # 3. Poisson arrivals at 0.8 x the saturation rate
+    lam = 0.8 * mu
+    arr = np.cumsum(np.random.Generator(np.random.PCG64(4548)).exponential(1.0 / lam, size=N))
+    lat, fin, arr, bad, st = run(N, arr)
     ctx.close()
-    ms = lambda v, q: round(float(np.percentile(np.array(v) * 1e3, q)), 3)
-    return {"requests": N, "sizes": f"cubes 16..{args.serve_max_n}", "mix": "Poisson/conv-diff 50/50, rtol 1e-6/1e-8",
-            "arrivals_per_s": round(lam, 2), "served": {"mode": "f32_refined, CUDA graphs",
-                                                        "slots": args.serve_slots,
-                                                        "solves_per_s": round(N / (max(fin) - arr[0]), 2),
-                                                        "p50_ms": ms(lat, 50), "p99_ms": ms(lat, 99),
-                                                        "failed": int(bad),
-                                                        "peak_admitted_bytes": int(sst["peak_in_use_bytes"]),
-                                                        "slot_busy_s": round(sst["busy_ms"] / 1e3, 3)},
-            "serial_fp64": {"solves_per_s": round(cap, 2), "p50_ms": ms(lat_ser, 50), "p99_ms": ms(lat_ser, 99)}}
+
+    def replay(arrivals):
+        end, out = 0.0, []
+        for a, s_ in zip(arrivals, serv):
+            end = max(a, end) + s_
+            out.append(end - a)
+        return np.array(out)
+
+    ms = lambda v, q: round(float(np.percentile(np.asarray(v) * 1e3, q)), 1)
+    arr_ser = np.cumsum(np.random.Generator(np.random.PCG64(4549)).exponential(1.0 / (0.8 * cap_ser), size=N))
+    lat_same, lat_own = replay(arr), replay(arr_ser)
+    return {"requests": N, "sizes": f"cubes {lo}..{hi} (edge uniform)", "mix": "Poisson/conv-diff 50/50, rtol 1e-6/1e-8",
+            "inputs": "drawn on the device at arrival (make_block recipe, torch generator)",
+            "served": {"mode": "f32_refined, CUDA graphs", "slots": slots,
+                       "saturation": {"requests": nsat, "solves_per_s": round(mu, 2), "seconds": round(float(fin_s.max()), 1),
+                                      "failed": int(bad_s)},
+                       "poisson_arrivals": {"arrivals_per_s": round(lam, 2), "load": "0.8 x saturation",
+                                            "solves_per_s": round(N / float(fin.max() - arr[0]), 2),
+                                            "wall_s": round(float(fin.max()), 1),
+                                            "p50_ms": ms(lat, 50), "p99_ms": ms(lat, 99), "failed": int(bad),
+                                            "peak_admitted_bytes": int(st["peak_in_use_bytes"]),
+                                            "slot_busy_s": round(st["busy_ms"] / 1e3, 1)}},
+            "serial_fp64": {"capacity_solves_per_s": round(cap_ser, 3),
+                            "service_time_sample": {"edges": edges, "classes": "poisson/convdiff x 1e-6/1e-8",
+                                                    "seconds": {f"{k}_{r:g}": [round(v, 3) for v in t]
+                                                                for (k, r), t in svc.items()}},
+                            "replay_same_arrivals": {"p50_ms": ms(lat_same, 50), "p99_ms": ms(lat_same, 99)},
+                            "replay_at_0.8_own_capacity": {"arrivals_per_s": round(0.8 * cap_ser, 3),
+                                                           "p50_ms": ms(lat_own, 50), "p99_ms": ms(lat_own, 99)}},
+            "vs_serial_fp64_capacity": round(mu / cap_ser, 2)}
 
 
 def main():

@@ -290,3 +290,57 @@ def pcorr_inputs(nx: int, ny: int, nz: int, seed: int, dirichlet_bottom: bool = 
         uz[0, :, :] = 0.0
     return PcorrInputs(nx, ny, nz, dx, dy, dz, rho, g, ux.reshape(-1).copy(), uy.reshape(-1).copy(),
                        uz.reshape(-1).copy(), dirichlet_bottom)
+
+
+def make_block_device(nx: int, ny: int, nz: int, seed: int, kind: str = "convdiff", device="cuda"):
+    """The ``make_block`` recipe drawn on a device with torch's seeded
+    generator (for request streams too large to draw on the host): the same
+    distributions and structure (D ~ U[0.5, 2] per interior face; convdiff: F ~
+    N(0, 1) per interior face, upwind, time term 0.01; poisson: a Dirichlet
+    bottom face with D ~ U[0.5, 2], no convection), x* ~ U[-1, 1], b = A x*.
+    The random streams differ from ``make_block``'s (torch's generator, not
+    PCG64).  Returns (coefs: list of the seven FP64 tensors in COEF_NAMES
+    order, b, xstar); for ``poisson`` aw, as, ab are returned too (the matrix is
+    symmetric)."""
+    import torch
+
+    if kind not in ("convdiff", "poisson"):
+        raise ValueError(f"unknown generator kind {kind!r}")
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    f64 = dict(dtype=torch.float64, device=device)
+
+    def U(shape):
+        return torch.rand(shape, generator=g, **f64) * 1.5 + 0.5
+
+    sx, sy, sz = _shapes(nx, ny, nz)
+    Dx, Dy, Dz = U(sx), U(sy), U(sz)
+    sh = (nz, ny, nx)
+    C = {k: torch.zeros(sh, **f64) for k in COEF_NAMES}
+    if kind == "convdiff":
+        Fx = torch.randn(sx, generator=g, **f64)
+        Fy = torch.randn(sy, generator=g, **f64)
+        Fz = torch.randn(sz, generator=g, **f64)
+        tt = 0.01
+    else:
+        Fx, Fy, Fz = torch.zeros(sx, **f64), torch.zeros(sy, **f64), torch.zeros(sz, **f64)
+        tt = 0.0
+    C["ae"][:, :, :-1] = -(Dx + torch.clamp(-Fx, min=0.0))
+    C["aw"][:, :, 1:] = -(Dx + torch.clamp(Fx, min=0.0))
+    C["an"][:, :-1, :] = -(Dy + torch.clamp(-Fy, min=0.0))
+    C["as"][:, 1:, :] = -(Dy + torch.clamp(Fy, min=0.0))
+    C["at"][:-1, :, :] = -(Dz + torch.clamp(-Fz, min=0.0))
+    C["ab"][1:, :, :] = -(Dz + torch.clamp(Fz, min=0.0))
+    ap = sum(C[k].abs() for k in COEF_NAMES[1:]) + tt
+    if kind == "poisson":
+        ap[0] += U((ny, nx))
+    C["ap"] = ap
+    xs = torch.rand(sh, generator=g, **f64) * 2.0 - 1.0
+    out = C["ap"] * xs
+    out[:, :, 1:] += C["aw"][:, :, 1:] * xs[:, :, :-1]
+    out[:, :, :-1] += C["ae"][:, :, :-1] * xs[:, :, 1:]
+    out[:, 1:, :] += C["as"][:, 1:, :] * xs[:, :-1, :]
+    out[:, :-1, :] += C["an"][:, :-1, :] * xs[:, 1:, :]
+    out[1:, :, :] += C["ab"][1:, :, :] * xs[:-1, :, :]
+    out[:-1, :, :] += C["at"][:-1, :, :] * xs[1:, :, :]
+    return [C[k].reshape(-1) for k in COEF_NAMES], out.reshape(-1), xs.reshape(-1)
