@@ -659,12 +659,14 @@ int oracle_solve_refined_mb(int nb, const int *dims, const double *const *A, con
  * -div(rho g grad p') = -div(rho u*) in finite volumes:
  *   interior face f between P and N:
  *     rho_f = (rho_P + rho_N) * 0.5,  g_f = (g_P + g_N) * 0.5,
- *     delta_f = (w_P + w_N) * 0.5  (w: the cells' widths along the face normal),
+ *     rdelta_f = 1 / ((w_P + w_N) * 0.5)  (w: the cells' widths along the
+ *       face normal; the reciprocal centre distance, a geometric factor of the
+ *       face that depends on one axis only),
  *     S_f = the face area (dy dz, dx dz or dx dy of P),
- *     A_N(P) = -(((rho_f * g_f) * S_f) / delta_f);
+ *     A_N(P) = -(((rho_f * g_f) * S_f) * rdelta_f);
  *   boundary faces are walls (coefficient 0), except the k = 0 face when
  *   dirichlet_bottom != 0 (p' = 0 beyond it): it adds
- *     cB = ((rho_P * g_P) * S_z) / (dz[0] * 0.5) to AP;
+ *     cB = ((rho_P * g_P) * S_z) * (1 / (dz[0] * 0.5)) to AP;
  *   AP = ((((((-AW) + (-AE)) + (-AS)) + (-AN)) + (-AB)) + (-AT)) + cB;
  *   mass fluxes F_f = (rho_f * u*_f) * S_f (boundary faces: rho_f = rho_P),
  *   b = -(((((F_e - F_w) + F_n) - F_s) + F_t) - F_b), the negative net outflow.
@@ -695,15 +697,15 @@ void oracle_assemble_pcorr(int nx, int ny, int nz, const double *dx, const doubl
           if (has[f]) {
             double rhof = (rho[p] + rho[nb[f]]) * 0.5;
             double gf = (g[p] + g[nb[f]]) * 0.5;
-            double delta = (wp[f] + w[f]) * 0.5;
-            c[f] = -(((rhof * gf) * S[f]) / delta);
+            double rdelta = 1.0 / ((wp[f] + w[f]) * 0.5);
+            c[f] = -(((rhof * gf) * S[f]) * rdelta);
             rf[f] = rhof;
           } else {
             rf[f] = rho[p];
           }
         }
         double cB = 0.0;
-        if (k == 0 && dirichlet_bottom) cB = ((rho[p] * g[p]) * Sz) / (dz[0] * 0.5);
+        if (k == 0 && dirichlet_bottom) cB = ((rho[p] * g[p]) * Sz) * (1.0 / (dz[0] * 0.5));
         aw[p] = c[0];
         ae[p] = c[1];
         as[p] = c[2];
