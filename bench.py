@@ -78,6 +78,8 @@ def parse(argv=None):
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-sat", type=int, default=500,
                     help="requests of the saturation run (a prefix of the request list)")
+    ap.add_argument("--serve-survey-prefix", type=int, default=400,
+                    help="requests served with arrivals at 0.8 x the serial FP64 capacity (a prefix; 0: skip)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-block batched-mesh measurement")
     ap.add_argument("--no-small", action="store_true", help="skip the 32^3 solve-latency measurement")
     ap.add_argument("--no-assembly", action="store_true", help="skip the pressure-correction assembly measurement")
@@ -788,7 +790,9 @@ def serving(args, local):
          requests: per-request latency (arrival -> result seen by the host),
          p50 / p99, solves/s.  The serial FP64 queue is replayed (FIFO, the
          interpolated service times) on the same arrivals and at 0.8 x its own
-         capacity.
+         capacity;
+      4. the first ``serve_survey_prefix`` requests with Poisson arrivals at
+         0.8 x the serial FP64 capacity, served and replayed serially.
     Server: FP32-refined mode, CUDA graphs, ``serve_slots`` slots, admitted
     by HBM footprint."""
     import numpy as np
@@ -884,6 +888,18 @@ def serving(args, local):
     lam = 0.8 * mu
     arr = np.cumsum(np.random.Generator(np.random.PCG64(4548)).exponential(1.0 / lam, size=N))
     lat, fin, arr, bad, st = run(N, arr)
+    # 4. a prefix of the list with arrivals at 0.8 x the serial FP64 capacity
+    #    (all 2000 at that rate would take ~20 minutes of arrivals)
+    npre = min(args.serve_survey_prefix, N)
+    pre = None
+    if npre > 0:
+        arr_p = np.cumsum(np.random.Generator(np.random.PCG64(4550)).exponential(1.0 / (0.8 * cap_ser), size=npre))
+        lat_p, fin_p, arr_p, bad_p, _ = run(npre, arr_p)
+        end, lat_sp = 0.0, []
+        for a_, s_ in zip(arr_p, serv[:npre]):
+            end = max(a_, end) + s_
+            lat_sp.append(end - a_)
+        pre = (npre, arr_p, lat_p, fin_p, bad_p, np.array(lat_sp))
     ctx.close()
 
     def replay(arrivals):
@@ -914,7 +930,13 @@ def serving(args, local):
                             "replay_same_arrivals": {"p50_ms": ms(lat_same, 50), "p99_ms": ms(lat_same, 99)},
                             "replay_at_0.8_own_capacity": {"arrivals_per_s": round(0.8 * cap_ser, 3),
                                                            "p50_ms": ms(lat_own, 50), "p99_ms": ms(lat_own, 99)}},
-            "vs_serial_fp64_capacity": round(mu / cap_ser, 2)}
+            "vs_serial_fp64_capacity": round(mu / cap_ser, 2),
+            "at_0.8_serial_capacity": None if pre is None else {
+                "requests": pre[0], "note": "the first requests of the list; arrivals at 0.8 x the serial FP64 capacity",
+                "arrivals_per_s": round(0.8 * cap_ser, 3),
+                "served": {"p50_ms": ms(pre[2], 50), "p99_ms": ms(pre[2], 99), "failed": int(pre[4]),
+                           "solves_per_s": round(pre[0] / float(pre[3].max() - pre[1][0]), 3)},
+                "serial_fp64_replay": {"p50_ms": ms(pre[5], 50), "p99_ms": ms(pre[5], 99)}}}
 
 
 def main():
