@@ -798,7 +798,7 @@ int sip_create(sip_ctx **out, int device, void *stream) {
     }
   }
   for (int kind = 0; kind < K_NKINDS; ++kind)
-    for (int Q : kQs)
+    for (int Q : {1, 2, 4})  // Q = 1: the factorisation's own decomposition
       for (int R : kRs) {
         const void *f = kernel_ptr(kind, Q, R);
         if (!f) continue;
@@ -1034,6 +1034,44 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
       }
   }
   std::vector<Tile> tiles_b(tiles.rbegin(), tiles.rend());
+  // The factorisation's own decomposition: 32 x kFacTK tiles, one row per
+  // warp.  Its steps are bound by the FP64 pipe of the SM sub-partitions (one
+  // warp instruction per 64 cycles each), so a step costs in proportion to
+  // the rows a sub-partition holds; one row per warp and 4 warps per tile
+  // keep that at one row and shorten the wavefront's chain, while several
+  // tiles share an SM where the wavefront is wide.
+  constexpr int kFacTK = 4;
+  std::vector<DevBlock> fdb;
+  std::vector<Tile> ftiles;
+  int fntiles = 0;
+  long long fface0 = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    DevBlock d = p->blocks[b].db;
+    d.TK = kFacTK;
+    d.nTK = (d.nz + kFacTK - 1) / kFacTK;
+    d.tile0 = fntiles;
+    d.nsteps_max = d.nx + kTJ + kFacTK - 2;
+    d.face0 = fface0;
+    d.face_tile_words = (long long)d.nsteps_max * (kTJ + kFacTK) * kFaceWordsMax;
+    const int nt = d.nTJ * d.nTK;
+    fntiles += nt;
+    fface0 += (long long)nt * d.face_tile_words;
+    fdb.push_back(d);
+  }
+  {
+    int maxwave = 0;
+    for (const DevBlock &d : fdb) maxwave = std::max(maxwave, d.nTJ + d.nTK - 2);
+    for (int w = 0; w <= maxwave; ++w)
+      for (int b = 0; b < nblocks; ++b) {
+        const DevBlock &d = fdb[b];
+        for (int ck = 0; ck < d.nTK; ++ck) {
+          const int cj = w - ck;
+          if (cj < 0 || cj >= d.nTJ) continue;
+          ftiles.push_back(Tile{b, cj, ck, d.tile0 + ck * d.nTJ + cj});
+        }
+      }
+  }
+  const long long face_words = std::max(face0, fface0);
 
   auto bail = [&](cudaError_t e, const char *what) {
     free_plan_memory(p);
@@ -1068,7 +1106,11 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
   PA(p->d_blocks, nblocks);
   PA(p->d_tiles_f, p->ntiles);
   PA(p->d_tiles_b, p->ntiles);
-  PA(p->faces, face0);
+  PA(p->faces, face_words);
+  DevBlock *d_fblocks = nullptr;
+  Tile *d_ftiles = nullptr;
+  PA(d_fblocks, nblocks);
+  PA(d_ftiles, fntiles);
   PA(p->partials, p->rowgrid);
   PA(p->bparts, p->nbparts);
   PA(p->ctl, 1);
@@ -1175,6 +1217,10 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
       tab.insert(tab.end(), bh.F.begin(), bh.F.end());
       hdb.push_back(bh.db);
     }
+    for (int b = 0; b < nblocks; ++b) {
+      fdb[b].PO = p->blocks[b].db.PO;
+      fdb[b].F = p->blocks[b].db.F;
+    }
     cudaError_t e = cudaMemcpyAsync(p->d_tab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(p->d_blocks, hdb.data(), hdb.size() * sizeof(DevBlock), cudaMemcpyHostToDevice, st);
@@ -1182,7 +1228,11 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
       e = cudaMemcpyAsync(p->d_tiles_f, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(p->d_tiles_b, tiles_b.data(), tiles_b.size() * sizeof(Tile), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->faces, 0, (size_t)face0 * sizeof(uint64_t), st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_fblocks, fdb.data(), fdb.size() * sizeof(DevBlock), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_ftiles, ftiles.data(), ftiles.size() * sizeof(Tile), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->faces, 0, (size_t)face_words * sizeof(uint64_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->ctl, 0, sizeof(Ctl), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->tickets, 0, 4 * sizeof(int), st);
@@ -1210,22 +1260,42 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
   {
     cudaError_t e = launch_set_ctl(p->ctl, -1.0, 0, st);
     if (e != cudaSuccess) return bail(e, "control");
+    // on the factorisation's own decomposition (one row per warp, kFacTK rows per tile)
+    auto run_factor = [&](int kind, auto &fp) -> cudaError_t {
+      fp.c = common(p, false, 2, 0, 0, kind);
+      fp.c.blocks = d_fblocks;
+      fp.c.tiles = d_ftiles;
+      fp.c.ntiles = fntiles;
+      fp.c.trace = nullptr;  // the trace buffer is sized for the sweeps' tiles
+      const int NTf = 32 * kFacTK;
+      int Rf = 3;
+      size_t smem = kernel_smem(kind, 1, Rf, NTf, p->tab_ints);
+      if (smem + ctx->kernel_static_smem > ctx->smem_optin) {
+        Rf = 2;
+        smem = kernel_smem(kind, 1, Rf, NTf, p->tab_ints);
+      }
+      const void *f = kernel_ptr(kind, 1, Rf);
+      const int cap = ctx->nsm * max_active(f, NTf, smem);
+      if (!f || cap < 1) return cudaErrorInvalidConfiguration;
+      const int grid = std::max(1, std::min(fntiles, cap));
+      void *args[] = {(void *)&fp};
+      ProfScope ps(p, kind);
+      return cudaLaunchKernel(f, dim3(grid), dim3(NTf), args, smem, st);
+    };
     if (f64) {
       FacParams<double> fp;
-      fp.c = common(p, false, 2, 0, 0, K_FACTOR);
       fp.a7 = a7;
       fp.recF = (double *)p->recF;
       fp.recB = (double *)p->recB;
       fp.alpha = opt.alpha;
-      e = launch(p, K_FACTOR, fp);
+      e = run_factor(K_FACTOR, fp);
     } else {
       FacParams<float> fp;
-      fp.c = common(p, false, 2, 0, 0, K_FACTOR32);
       fp.a7 = a7;
       fp.recF = (float *)p->recF;
       fp.recB = (float *)p->recB;
       fp.alpha = opt.alpha;
-      e = launch(p, K_FACTOR32, fp);
+      e = run_factor(K_FACTOR32, fp);
     }
     if (e != cudaSuccess) return bail(e, "factor launch");
     int rc = check_status(p);
@@ -1236,6 +1306,8 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
       return fail(ctx, rc, msg);
     }
     pfree(p, a7, (size_t)N * 8 * sizeof(double));
+    pfree(p, d_ftiles, (size_t)std::max(fntiles, 1) * sizeof(Tile));
+    pfree(p, d_fblocks, (size_t)nblocks * sizeof(DevBlock));
   }
   *out = p;
   return SIP_OK;
