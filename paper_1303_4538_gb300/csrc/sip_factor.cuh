@@ -19,6 +19,15 @@ namespace sipk {
 // 1/(dB dW dS), the U entries through 1/LP; FP64 throughput bounds the steps).
 // Arithmetic in FP64; stored (as TF) into the L record [LB LW LS 1/LP] and
 // the U record [UE UN UT 0].  Faces carry (UN, UE, UT): 48 bytes.
+// IEEE-754 binary64 tests on the exponent field with integer instructions
+// (they keep the FP64 pipe, which bounds this kernel, for the arithmetic):
+// finite: exponent field not all ones; in range: |x| within [2^-930, 2^930)
+__device__ __forceinline__ bool finite64(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff; }
+__device__ __forceinline__ bool midrange64(double x) {
+  const int e = (__double2hiint(x) >> 20) & 0x7ff;  // biased exponent
+  return e > 1023 - 930 && e < 1023 + 930;
+}
+
 template <typename TF, int Q, int R>
 __global__ void __launch_bounds__(512) k_factor(FacParams<TF> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -150,12 +159,12 @@ __global__ void __launch_bounds__(512) k_factor(FacParams<TF> P) {
         const double dS = 1.0 + al * (ueS + utS);
         // one division for the three quotients: each is the other two
         // denominators times 1/(dB dW dS), within a few ulps; exact quotients
-        // when that product leaves the normal range (or is not finite)
+        // when that product lies outside [2^-930, 2^930) (or is not finite)
         double LB, LW, LS;
         {
           const double dBW = dB * dW;
           const double pr = dBW * dS;
-          if (fabs(pr) > 1e-280 && fabs(pr) < 1e280) {
+          if (midrange64(pr)) {
             const double rq = 1.0 / pr;
             LB = ab * ((dW * dS) * rq);
             LW = aw * ((dB * dS) * rq);
@@ -179,8 +188,8 @@ __global__ void __launch_bounds__(512) k_factor(FacParams<TF> P) {
           UN = (an - P1) * RLP;
           UE = (ae - P2) * RLP;
           UT = (at - P3) * RLP;
-          if (LP == 0.0 || !isfinite(RLP) || !isfinite(LB) || !isfinite(LW) || !isfinite(LS) ||
-              !isfinite(UN) || !isfinite(UE) || !isfinite(UT) || !isfinite(LP))
+          if (LP == 0.0 || !finite64(RLP) || !finite64(LB) || !finite64(LW) || !finite64(LS) ||
+              !finite64(UN) || !finite64(UE) || !finite64(UT) || !finite64(LP))
             atomicCAS(c.status, DEV_OK, DEV_BREAKDOWN);
           const long long cell = B.cell0 + rb(g.s0 + t, g.k(q)) + g.j;
           TF *fr = P.recF + cell * 4;
