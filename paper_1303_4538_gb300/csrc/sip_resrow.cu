@@ -39,6 +39,17 @@ __device__ __forceinline__ int ld_status(const int *p) {
 
 constexpr int kRowThreads = 256;
 
+// the first four values of an A record (16-byte aligned: 16 B in FP32, 32 B
+// in FP64) with vector loads
+__device__ __forceinline__ void ld_rec4(const float *a, float v[4]) {
+  const float4 t = *reinterpret_cast<const float4 *>(a);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld_rec4(const double *a, double v[4]) {
+  const double2 t0 = reinterpret_cast<const double2 *>(a)[0], t1 = reinterpret_cast<const double2 *>(a)[1];
+  v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+}
+
 template <typename TA, typename TX, typename TR, bool SYM, bool NORM>
 __global__ void __launch_bounds__(kRowThreads, 4) k_resrow(RowParams<TA, TX, TR> P) {
   using TC = TX;  // arithmetic precision: that of the iterate
@@ -102,16 +113,20 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_resrow(RowParams<TA, TX, TR>
       const TC xn = hn ? (TC)Xb[bE + j + 1] : TC(0);
       const TC xb = hb ? (TC)Xb[bB + j] : TC(0);
       const TC xt = ht ? (TC)Xb[bT + j] : TC(0);
-      const TC ap = (TC)a[0], ae = (TC)a[OAE], an = (TC)a[OAN], at = (TC)a[OAT];
-      TC aw, as, ab;
+      TC ap, ae, an, at, aw, as, ab;
       if constexpr (SYM) {
+        TA v[4];
+        ld_rec4(a, v);  // [AP AE AN AT]
+        ap = (TC)v[0]; ae = (TC)v[1]; an = (TC)v[2]; at = (TC)v[3];
         aw = hw ? (TC)Ab[(size_t)(bW + j) * NA + OAE] : TC(0);
         as = hs ? (TC)Ab[(size_t)(bW + j - 1) * NA + OAN] : TC(0);
         ab = hb ? (TC)Ab[(size_t)(bB + j) * NA + OAT] : TC(0);
       } else {
-        aw = (TC)a[1];
-        as = (TC)a[3];
-        ab = (TC)a[5];
+        TA v[8];
+        ld_rec4(a, v);  // [AP AW AE AS AN AB AT 0]
+        ld_rec4(a + 4, v + 4);
+        ap = (TC)v[0]; aw = (TC)v[1]; ae = (TC)v[2]; as = (TC)v[3];
+        an = (TC)v[4]; ab = (TC)v[5]; at = (TC)v[6];
       }
       r = fma(-ap, x0, r);
       r = fma(-aw, xw, r);
