@@ -533,7 +533,8 @@ def small(args, local):
     b = torch.from_numpy(blk.b).cuda()
     x = torch.zeros(blk.n, dtype=torch.float64, device="cuda")
     desc = sip.make_desc(blk.nx, blk.ny, blk.nz, A, b, x)
-    out = {"workload": "convdiff_32cube", "cells": blk.n, "alpha": 0.92, "rtol": 1e-8, "solves": args.small_solves}
+    out = {"workload": "convdiff_32cube", "cells": blk.n, "alpha": 0.92, "rtol": 1e-8, "solves": args.small_solves,
+           "f32_refined_inner_iters": 4}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for name, mode in (("f64", sip.SIP_MODE_F64), ("f32_refined", sip.SIP_MODE_F32_REFINED)):
         plan = sip.Plan(ctx, [desc], sip.default_options(mode=mode, graphs=1))
@@ -914,7 +915,7 @@ def serving(args, local):
     lat_same, lat_own = replay(arr), replay(arr_ser)
     return {"requests": N, "sizes": f"cubes {lo}..{hi} (edge uniform)", "mix": "Poisson/conv-diff 50/50, rtol 1e-6/1e-8",
             "inputs": "drawn on the device at arrival (make_block recipe, torch generator)",
-            "served": {"mode": "f32_refined, CUDA graphs", "slots": slots,
+            "served": {"mode": "f32_refined (4 FP32 iterations per correction), CUDA graphs", "slots": slots,
                        "saturation": {"requests": nsat, "solves_per_s": round(mu, 2), "seconds": round(float(fin_s.max()), 1),
                                       "failed": int(bad_s)},
                        "poisson_arrivals": {"arrivals_per_s": round(lam, 2), "load": "0.8 x saturation",
