@@ -78,7 +78,7 @@ def parse(argv=None):
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-sat", type=int, default=500,
                     help="requests of the saturation run (a prefix of the request list)")
-    ap.add_argument("--serve-survey-prefix", type=int, default=400,
+    ap.add_argument("--serve-capacity-prefix", type=int, default=400,
                     help="requests served with arrivals at 0.8 x the serial FP64 capacity (a prefix; 0: skip)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-block batched-mesh measurement")
     ap.add_argument("--no-small", action="store_true", help="skip the 32^3 solve-latency measurement")
@@ -792,7 +792,7 @@ def serving(args, local):
          p50 / p99, solves/s.  The serial FP64 queue is replayed (FIFO, the
          interpolated service times) on the same arrivals and at 0.8 x its own
          capacity;
-      4. the first ``serve_survey_prefix`` requests with Poisson arrivals at
+      4. the first ``serve_capacity_prefix`` requests with Poisson arrivals at
          0.8 x the serial FP64 capacity, served and replayed serially.
     Server: FP32-refined mode, CUDA graphs, ``serve_slots`` slots, admitted
     by HBM footprint."""
@@ -891,7 +891,7 @@ def serving(args, local):
     lat, fin, arr, bad, st = run(N, arr)
     # 4. a prefix of the list with arrivals at 0.8 x the serial FP64 capacity
     #    (all 2000 at that rate would take ~20 minutes of arrivals)
-    npre = min(args.serve_survey_prefix, N)
+    npre = min(args.serve_capacity_prefix, N)
     pre = None
     if npre > 0:
         arr_p = np.cumsum(np.random.Generator(np.random.PCG64(4550)).exponential(1.0 / (0.8 * cap_ser), size=npre))
