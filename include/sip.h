@@ -193,6 +193,18 @@ int sip_export_factors(sip_plan *plan, int blk, double *const out[7]);
  * ascends within a row.  Entries of empty rows are INT32_MIN. */
 int sip_plane_layout(int nx, int ny, int nz, int32_t *rbT);
 
+/* Launch model of the tile-shape chooser (host-only helper, no device
+ * needed): the modelled duration, in SM cycles (*cycles_out, host), of one
+ * forward or backward sweep launch over `nblocks` blocks (dims: host,
+ * nx ny nz per block) cut into 32 x (rows_per_thread * warps) column tiles
+ * that `ctas` resident CTAs on `nsm` SMs claim in the launch's order
+ * (anti-diagonal waves, blocks interleaved).  fp64 = 1: FP64 sweeps, 0: FP32.
+ * The tile wavefront is the one of the hyperplane ordering of Sec. 2; the
+ * per-step cost is fitted on GB300.  SIP_ERR_INVALID_ARG for dims < 1, a
+ * rows_per_thread outside {1, 2, 4}, warps outside 1..16, ctas or nsm < 1. */
+int sip_tile_model(const int32_t *dims, int nblocks, int rows_per_thread, int warps, int ctas, int nsm, int fp64,
+                   double *cycles_out);
+
 /* ||b - A x||_2 (*rnorm_out) and ||b||_2 (*bnorm_out) of one block, computed
  * directly on the descriptor's natural-layout arrays (the residual of
  * resforward3d, Sec. 4.1 / Table 1, without a plan): FP64 arithmetic (FP32

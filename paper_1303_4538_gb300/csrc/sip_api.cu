@@ -556,18 +556,14 @@ std::vector<int> plan_kinds(int mode) {
 }
 
 // Tile shape: rows per thread Q and warps NW (tile = 32 x Q*NW), stage depth
-// R.  A sweep's time is (steps on its critical path) x (time of one step).
-// The critical path of a block walks the tile chain to its last tile, each
-// hop lagging by the tile's extent plus the start slack, then that tile's own
-// walk: (nTJ-1)(32 + lead) + (nTK-1)(TK + lead) + nx + 32 + TK - 2 steps.  A
-// step is latency-bound and grows with the warps resident on an SM (they
-// share the SM's load/store pipe): measured on GB300 (256^3 and 128^3
-// Poisson blocks, every shape) as 1 + beta x warps per SM with beta = 0.04
-// for the FP32 sweeps and 0.057 for FP64, and 1.45x longer with four rows per
-// thread than with two at the same TK.  Only shapes whose tiles are all
-// resident at once are taken (else the fewest waves); R = 3 unless forced
-// (deeper rings measured slower on GB300: 3 beat 4 by up to 11 % and 6 is
-// slower still).
+// R.  Shapes are ranked by the launch model of sip_shape.cu (the tile
+// wavefront replayed with a fitted per-step cost that grows with the warps
+// sharing an SM).  Automatic choices take one or two rows per thread (four
+// measured 1.45x the step of two) with an even number of warps for one row
+// (a balanced split over the four sub-partitions), up to 16 warps with one
+// row and 12 with two (16 x 2 measured slower than modelled at 384^3); R = 3
+// unless forced (deeper rings measured slower on GB300: 3 beat 4 by up to
+// 11 %, 6 is slower still, and the start slack of a tile grows with R).
 struct ShapeChoice {
   int Q = 0, NW = 0, ntiles = 0;
   int R[K_NKINDS] = {}, cap[K_NKINDS] = {};
@@ -577,18 +573,19 @@ struct ShapeChoice {
 std::vector<ShapeChoice> shape_candidates(sip_ctx *ctx, const std::vector<BlockHost> &blocks,
                                           const std::vector<int> &kinds, int tab_ints, int forceTK, int forceR,
                                           int forceQ, bool fp64) {
-  const double beta = fp64 ? 0.057 : 0.04;
+  std::vector<int> dims;
+  for (auto &bh : blocks) dims.insert(dims.end(), {bh.d.nx, bh.d.ny, bh.d.nz});
   std::vector<ShapeChoice> all;
   for (int Q : kQs)
     for (int NW = 1; NW <= 16; ++NW) {
       const int TK = Q * NW, NT = 32 * NW;
       if (forceTK > 0 && TK != forceTK) continue;
       if (forceQ > 0 && Q != forceQ) continue;
-      if (forceQ == 0 && forceTK == 0 && Q != 2) continue;  // 2 rows per thread measured fastest
-      // the model was fitted up to 8 warps per tile; 16 measured slower than
-      // it predicts (384^3 FP64: 32 x 32 tiles 5.85 ms per iteration, 32 x 24
-      // 4.85 ms), so automatic choices stop at 12
-      if (forceTK == 0 && NW > 12) continue;
+      if (forceQ == 0 && forceTK == 0) {
+        if (Q == 4) continue;
+        if (Q == 1 && NW % 2) continue;
+        if (Q == 2 && NW > 12) continue;
+      }
       ShapeChoice c;
       c.Q = Q;
       c.NW = NW;
@@ -614,21 +611,11 @@ std::vector<ShapeChoice> shape_candidates(sip_ctx *ctx, const std::vector<BlockH
         capmin = std::min(capmin, bcap);
       }
       if (!ok) continue;
-      long long steps = 0;
-      for (auto &bh : blocks) {
-        const int nTJ = (bh.d.ny + kTJ - 1) / kTJ, nTK = (bh.d.nz + TK - 1) / TK;
-        c.ntiles += nTJ * nTK;
-        const int R = c.R[kinds[1]];
-        // hop slack of the fitted model (the per-step factor beta was fitted with it)
-        const int lead = std::min(R + 1, std::max(bh.d.nx - 1, 0));
-        steps = std::max(steps, (long long)(nTJ - 1) * (kTJ + lead) + (long long)(nTK - 1) * (TK + lead) +
-                                    bh.d.nx + kTJ + TK - 2);
-      }
-      const int waves = (c.ntiles + capmin - 1) / capmin;
-      // warps per SM, averaged: a few SMs holding a second tile cost a little
-      const double per_sm = (double)NW * std::max(1.0, (double)c.ntiles / ctx->nsm);
-      // four rows per thread: measured 1.45x the step time of two at equal TK
-      c.score = (double)steps * (1.0 + beta * per_sm) * (Q == 4 ? 1.45 : 1.0) * waves * (waves > 1 ? 4.0 : 1.0);
+      for (auto &bh : blocks) c.ntiles += ((bh.d.ny + kTJ - 1) / kTJ) * ((bh.d.nz + TK - 1) / TK);
+      c.score = sweep_model_cycles(dims.data(), (int)blocks.size(), Q, NW, capmin, ctx->nsm, fp64);
+      // deeper rings lengthen the start slack of every tile
+      const int R = c.R[kinds[1]];
+      if (R > 3) c.score *= 1.0 + 0.03 * (R - 3);
       all.push_back(c);
     }
   std::stable_sort(all.begin(), all.end(), [](const ShapeChoice &a, const ShapeChoice &b) { return a.score < b.score; });
@@ -906,8 +893,8 @@ int sip_factor(sip_ctx *ctx, const sip_block_desc *blocks, int nblocks, const si
     return fail(ctx, SIP_ERR_INVALID_ARG, "tile_k must be 0 (auto) or an even number <= 64");
   if (opt.stages != 0 && opt.stages != 3 && opt.stages != 4 && opt.stages != 6)
     return fail(ctx, SIP_ERR_INVALID_ARG, "stages must be 0 (auto), 3, 4 or 6");
-  if (opt.rows_per_thread != 0 && opt.rows_per_thread != 2 && opt.rows_per_thread != 4)
-    return fail(ctx, SIP_ERR_INVALID_ARG, "rows_per_thread must be 0 (auto), 2 or 4");
+  if (opt.rows_per_thread != 0 && opt.rows_per_thread != 1 && opt.rows_per_thread != 2 && opt.rows_per_thread != 4)
+    return fail(ctx, SIP_ERR_INVALID_ARG, "rows_per_thread must be 0 (auto), 1, 2 or 4");
   if (opt.autotune != 0 && opt.autotune != 1) return fail(ctx, SIP_ERR_INVALID_ARG, "autotune must be 0 or 1");
   if (opt.autotune && opt.tile_k == 0 && opt.rows_per_thread == 0 && opt.stages == 0) {
     const std::string sig = tune_signature(ctx, blocks, nblocks, opt);
@@ -1422,6 +1409,16 @@ int sip_plane_layout(int nx, int ny, int nz, int32_t *rbT) {
       const bool row = m >= 0 && m <= mmax && std::max(0, m - (nx - 1)) <= std::min(ny - 1, m);
       rbT[(size_t)k * np + s] = row ? plane_row_base(PO.data(), F.data(), mmax, nx, s, k) : INT32_MIN;
     }
+  return SIP_OK;
+}
+
+int sip_tile_model(const int32_t *dims, int nblocks, int rows_per_thread, int warps, int ctas, int nsm, int fp64,
+                   double *cycles_out) {
+  if (!dims || !cycles_out || nblocks < 1 || warps < 1 || warps > 16 || ctas < 1 || nsm < 1) return SIP_ERR_INVALID_ARG;
+  if (rows_per_thread != 1 && rows_per_thread != 2 && rows_per_thread != 4) return SIP_ERR_INVALID_ARG;
+  const double c = sweep_model_cycles(dims, nblocks, rows_per_thread, warps, ctas, nsm, fp64 != 0);
+  if (c < 0) return SIP_ERR_INVALID_ARG;
+  *cycles_out = c;
   return SIP_OK;
 }
 

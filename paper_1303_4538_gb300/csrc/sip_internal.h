@@ -236,4 +236,9 @@ cudaError_t launch_assemble_pcorr(const PcorrArgs &a, int grid, cudaStream_t st)
 constexpr int FIN_BNORM = 0;   // partials are ||b||^2 pieces: set ctl->bnorm
 constexpr int FIN_RELRES = 1;  // partials are ||r||^2 pieces: relres, stop rule, counters
 
+// Modelled duration (SM cycles) of one sweep launch over blocks of dims
+// (nx, ny, nz per block) with 32 x (Q NW) tiles, `ctas` resident CTAs on
+// `nsm` SMs (sip_shape.cu); -1 on a bad argument.
+double sweep_model_cycles(const int *dims, int nblocks, int Q, int NW, int ctas, int nsm, bool fp64);
+
 }  // namespace sipk

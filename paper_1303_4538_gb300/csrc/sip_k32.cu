@@ -26,7 +26,7 @@ static const void *pickfac1_float(int kind) {
 }
 
 const void *kernel_ptr_32(int kind, int Q, int R) {
-  if (Q == 1) return R == 2 ? pickfac1_float<2>(kind) : R == 3 ? pickfac1_float<3>(kind) : nullptr;
+  if (Q == 1) return R == 2 ? pickfac1_float<2>(kind) : R == 3 ? pick32<1, 3>(kind) : R == 4 ? pick32<1, 4>(kind) : R == 6 ? pick32<1, 6>(kind) : nullptr;
   if (Q == 2) return R == 2 ? pick32<2, 2>(kind) : R == 3 ? pick32<2, 3>(kind) : R == 4 ? pick32<2, 4>(kind) : R == 6 ? pick32<2, 6>(kind) : nullptr;
   if (Q == 4) return R == 2 ? pick32<4, 2>(kind) : R == 3 ? pick32<4, 3>(kind) : R == 4 ? pick32<4, 4>(kind) : R == 6 ? pick32<4, 6>(kind) : nullptr;
   return nullptr;

@@ -24,7 +24,7 @@ static const void *pickfac1_double(int kind) {
 }
 
 const void *kernel_ptr_64(int kind, int Q, int R) {
-  if (Q == 1) return R == 2 ? pickfac1_double<2>(kind) : R == 3 ? pickfac1_double<3>(kind) : nullptr;
+  if (Q == 1) return R == 2 ? pickfac1_double<2>(kind) : R == 3 ? pick64<1, 3>(kind) : R == 4 ? pick64<1, 4>(kind) : R == 6 ? pick64<1, 6>(kind) : nullptr;
   if (Q == 2) return R == 2 ? pick64<2, 2>(kind) : R == 3 ? pick64<2, 3>(kind) : R == 4 ? pick64<2, 4>(kind) : R == 6 ? pick64<2, 6>(kind) : nullptr;
   if (Q == 4) return R == 2 ? pick64<4, 2>(kind) : R == 3 ? pick64<4, 3>(kind) : R == 4 ? pick64<4, 4>(kind) : R == 6 ? pick64<4, 6>(kind) : nullptr;
   return nullptr;

@@ -24,7 +24,7 @@ enum KernelKind {
   K_NKINDS
 };
 
-constexpr int kQs[2] = {2, 4};
+constexpr int kQs[3] = {1, 2, 4};
 constexpr int kRs[4] = {2, 3, 4, 6};  // 2: the factorisation only (wide tiles)
 
 // sweep kernel of a kind (nullptr for the row kinds)

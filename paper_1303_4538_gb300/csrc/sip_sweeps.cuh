@@ -163,41 +163,62 @@ __device__ __forceinline__ bool rec_ok(const uint64_t (&w)[W], unsigned expect) 
   return ok;
 }
 
-// Poll a W-word record in L2 until every tag equals `expect`.  Returns false
-// (and zero words) after max_spin polls or once another thread recorded an
-// error; `abort` then stays set so this thread never waits again.
+// Poll a W-word record in L2 until every tag equals `expect`.  Gives up
+// (zero words, abort set) after max_spin polls or once another thread
+// recorded an error.  The slow path is kept out of line and returns its
+// words by value: a caller's record array whose address reached an
+// out-of-line call would have to live in local memory on the fast path too.
 template <int W>
-__device__ __noinline__ bool face_wait(const uint64_t *p, unsigned expect, uint64_t (&w)[W],
-                                       const SweepCommon &c, bool &abort, unsigned long long *tr) {
+struct Polled {
+  uint64_t w[W];
+  bool abort;
+};
+template <int W>
+__device__ __noinline__ Polled<W> face_poll(const uint64_t *p, unsigned expect, const SweepCommon &c, bool abort,
+                                            unsigned long long *tr) {
+  Polled<W> o;
+  o.abort = abort;
   if (!abort) {
     long long spins = 0;
     const unsigned long long t0 = tr ? gtimer() : 0ull;
     for (;;) {
 #pragma unroll
-      for (int q = 0; q < W; ++q) w[q] = ld_relaxed(p + q);
-      if (rec_ok<W>(w, expect)) {
+      for (int q = 0; q < W; ++q) o.w[q] = ld_relaxed(p + q);
+      if (rec_ok<W>(o.w, expect)) {
         if (tr) {
           atomicAdd(tr + 3, 1ull);
           atomicAdd(tr + 4, gtimer() - t0);
         }
-        return true;
+        return o;
       }
       ++spins;
       if (spins > c.max_spin) {
         atomicCAS(c.status, DEV_OK, DEV_TIMEOUT);
-        abort = true;
+        o.abort = true;
         break;
       }
       if ((spins & 63) == 0 && ld_relaxed(c.status) != DEV_OK) {
-        abort = true;
+        o.abort = true;
         break;
       }
       __nanosleep(32);
     }
   }
 #pragma unroll
-  for (int q = 0; q < W; ++q) w[q] = 0;
-  return false;
+  for (int q = 0; q < W; ++q) o.w[q] = 0;
+  return o;
+}
+
+// Returns false (and zero words) when the wait gave up; `abort` then stays
+// set so this thread never waits again.
+template <int W>
+__device__ __forceinline__ bool face_wait(const uint64_t *p, unsigned expect, uint64_t (&w)[W],
+                                          const SweepCommon &c, bool &abort, unsigned long long *tr) {
+  const Polled<W> o = face_poll<W>(p, expect, c, abort, tr);
+#pragma unroll
+  for (int q = 0; q < W; ++q) w[q] = o.w[q];
+  abort = o.abort;
+  return !o.abort;
 }
 
 // Take the record staged in shared memory; re-read it from L2 if it is stale.
@@ -366,7 +387,7 @@ __device__ __forceinline__ void face_put(uint64_t *p, const T (&v)[Q], int q, un
 // warp's row-base chunk, one shuffle per row; the cell offsets are kept in the
 // stage for the store) and computes step t from its stage.
 template <typename T, int Q, int R>
-__global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
+__global__ void __launch_bounds__(512, 1) k_forward(FwdParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_claim, s_blk;
   constexpr int W = 2;
@@ -562,7 +583,7 @@ __global__ void __launch_bounds__(512) k_forward(FwdParams<T> P) {
 // (descending planes), x_P <- x_P + d_P.  ZX: x = 0 on entry (x_P <- d_P).
 // Backward step u processes local plane t = last - u.
 template <typename T, bool ZX, int Q, int R>
-__global__ void __launch_bounds__(512) k_backward(BwdParams<T> P) {
+__global__ void __launch_bounds__(512, 1) k_backward(BwdParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_claim, s_blk;
   constexpr int W = 2;

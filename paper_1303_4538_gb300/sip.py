@@ -44,7 +44,7 @@ EXPORTED = (
     "sip_plan_destroy", "sip_plane_layout", "sip_profile_enable", "sip_profile_read",
     "sip_launch_count", "sip_kernel_name", "sip_residual_norm",
     "sip_residual_norm_noalloc", "sip_server_start", "sip_server_submit", "sip_server_poll", "sip_server_stop",
-    "sip_server_get_stats", "sip_assemble_pcorr",
+    "sip_server_get_stats", "sip_assemble_pcorr", "sip_tile_model",
 )
 
 
@@ -342,6 +342,19 @@ def plane_layout(nx: int, ny: int, nz: int):
     if rc != SIP_OK:
         raise SipError(rc, "sip_plane_layout failed")
     return out
+
+
+def tile_model(dims, rows_per_thread: int, warps: int, ctas: int, nsm: int = 152, fp64: bool = False) -> float:
+    """Modelled SM cycles of one sweep launch (host only, no GPU needed):
+    dims = [(nx, ny, nz), ...], tiles of 32 x (rows_per_thread * warps)."""
+    import numpy as np
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(-1, 3))
+    out = ctypes.c_double()
+    rc = lib().sip_tile_model(d.ctypes.data_as(ctypes.c_void_p), int(d.shape[0]), int(rows_per_thread), int(warps),
+                              int(ctas), int(nsm), int(bool(fp64)), ctypes.byref(out))
+    if rc != SIP_OK:
+        raise SipError(rc, "sip_tile_model failed")
+    return out.value
 
 
 class Server:
