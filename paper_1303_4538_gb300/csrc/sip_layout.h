@@ -4,9 +4,8 @@
 // Every sweep kernel's dynamic shared memory is
 //   [ PO + F tables of the current block ]
 //   [ R stages: per step the staged records of the thread's Q rows, then
-//     scalar slots (r; y and x), then the
-//     cells' block-local offsets (kept from the issue for the store) ]
-//   [ exchange between neighbouring warps, double buffered ]
+//     scalar slots (r; y and x) ]
+//   [ exchange between neighbouring warps, one slot per stage ]
 //   [ R stages of face records consumed by the tile's edge threads ]
 #pragma once
 #include <cstddef>
@@ -19,7 +18,6 @@ struct SweepLayout {
   size_t tab;    // bytes of the PO/F tables
   size_t step;   // bytes of one stage
   size_t rec;    // bytes of the staged records inside a stage (Q * NT * rsb)
-  size_t off;    // offset inside a stage of the cells' block-local offsets (Q * NT ints)
   size_t exch;   // bytes of the exchange area
   size_t faces;  // bytes of the face ring
   size_t total;
@@ -38,9 +36,8 @@ __host__ __device__ inline SweepLayout fwd_layout(int esize, int Q, int R, int N
   L.fs = TK + 32;
   L.tab = lay_a16((size_t)tab_ints * 4);
   L.rec = (size_t)Q * NT * L.rsb;
-  L.off = L.rec + (size_t)L.nsv * NT * esize;
-  L.step = lay_a16(L.off + (size_t)Q * NT * 4);
-  L.exch = lay_a16((size_t)2 * NW * 32 * esize);
+  L.step = lay_a16(L.rec + (size_t)L.nsv * NT * esize);
+  L.exch = lay_a16((size_t)R * NW * 32 * esize);
   L.faces = (size_t)R * L.fs * 2 * 8;
   L.total = L.tab + (size_t)R * L.step + L.exch + L.faces;
   return L;
@@ -55,9 +52,8 @@ __host__ __device__ inline SweepLayout bwd_layout(int esize, bool zx, int Q, int
   L.fs = TK + 32;
   L.tab = lay_a16((size_t)tab_ints * 4);
   L.rec = (size_t)Q * NT * L.rsb;
-  L.off = L.rec + (size_t)L.nsv * NT * esize;
-  L.step = lay_a16(L.off + (size_t)Q * NT * 4);
-  L.exch = lay_a16((size_t)2 * NW * 32 * esize);
+  L.step = lay_a16(L.rec + (size_t)L.nsv * NT * esize);
+  L.exch = lay_a16((size_t)R * NW * 32 * esize);
   L.faces = (size_t)R * L.fs * 2 * 8;
   L.total = L.tab + (size_t)R * L.step + L.exch + L.faces;
   return L;

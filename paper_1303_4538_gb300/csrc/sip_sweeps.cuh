@@ -15,7 +15,7 @@
 //   * neighbours of the previous (next) plane: W/E from the thread's own
 //     registers, S/N from lanes j -+ 1 by warp shuffles, B/T from the
 //     thread's own neighbouring row, and across warps through a
-//     double-buffered shared-memory exchange (one barrier per step);
+//     shared-memory exchange with one slot per stage (one barrier per step);
 //   * each cell's static data (factors, or A for the factorisation) is one
 //     16-byte aligned record, staged with cp.async.cg (L2 only) R-1 steps
 //     ahead into a ring of shared-memory stages together with the cell's
@@ -41,11 +41,21 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <type_traits>
 
 #include "sip_internal.h"
 #include "sip_layout.h"
 
 namespace sipk {
+
+// Compile-time loop: f(std::integral_constant<int, U>{}) for U = B .. E - 1.
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F &&f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
@@ -404,7 +414,7 @@ __global__ void __launch_bounds__(512, 1) k_forward(FwdParams<T> P) {
   const SweepLayout L = fwd_layout((int)sizeof(T), Q, R, NT, c.tab_ints);
   int *sPO = reinterpret_cast<int *>(smem_raw);
   unsigned char *stage = smem_raw + L.tab;
-  T *exB = reinterpret_cast<T *>(stage + (size_t)R * L.step);  // [2][NW][32]: y of a warp's last row
+  T *exB = reinterpret_cast<T *>(stage + (size_t)R * L.step);  // [R][NW][32]: y of a warp's last row
   uint64_t *fst = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(exB) + L.exch);
   const int FS = L.fs;
   bool abort = false;
@@ -451,36 +461,35 @@ __global__ void __launch_bounds__(512, 1) k_forward(FwdParams<T> P) {
     uint64_t *pjn = myf + (long long)w * Q * W;
     uint64_t *pkn = myf + kface + (long long)lane * W;
 
-    auto issue = [&](int tt) {
+    // Step t uses stage slot, exchange slot and store-offset registers
+    // t % R: the step loop is unrolled by R, so every slot index is a
+    // compile-time constant and the offsets never leave registers.
+    int offr[R][Q];
+    auto issue = [&](int tt, auto slot) {
+      constexpr int sl = decltype(slot)::value;
       if (tt < g.nsteps) {
         if (tt - cb >= C) {
           cb += C;
           chunk = rowbase_chunk<Q>(B, sPO, sF, g.s0, kchunk, cb + lane / Q, g.nsteps);
         }
-        const int sl = tt % R;
         unsigned char *st = stage + (size_t)sl * L.step;
         T *sr = reinterpret_cast<T *>(st + L.rec) + tid;
-        int *so = reinterpret_cast<int *>(st + L.off) + tid;
         uint64_t *fs = fst + (size_t)sl * FS * W;
-        // addresses of every row first, then the copies (the copies are
-        // ordered memory operations; keeping them together lets the
-        // address arithmetic of all rows overlap)
-        int off[Q];
+        // addresses of every row first, then the copies
         bool v[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          off[q] = __shfl_sync(0xffffffffu, chunk, (tt - cb) * Q + q) + g.j;
+          offr[sl][q] = __shfl_sync(0xffffffffu, chunk, (tt - cb) * Q + q) + g.j;
           v[q] = colq[q] && (unsigned)(tt - tlo[q]) < nxu;
         }
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          const int o = v[q] ? off[q] : 0;
+          const int o = v[q] ? offr[sl][q] : 0;
           unsigned char *d = st + ((size_t)q * NT + tid) * RBY;
           const unsigned char *src = reinterpret_cast<const unsigned char *>(recb + (size_t)o * 4);
 #pragma unroll
           for (int z = 0; z < RBY / 16; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v[q]);
           cp_async_zfill<sizeof(T)>(sr + q * NT, rb + o, v[q]);
-          so[q * NT] = off[q];
         }
 #pragma unroll
         for (int q = 0; q < Q; q += PJ) {
@@ -494,83 +503,85 @@ __global__ void __launch_bounds__(512, 1) k_forward(FwdParams<T> P) {
       }
       cp_async_commit();
     };
-#pragma unroll
-    for (int tt = 0; tt < R - 1; ++tt) issue(tt);
+    static_for<0, R - 1>([&](auto u) { issue(decltype(u)::value, u); });
 
     T ym1[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) ym1[q] = T(0);
-    for (int t = 0; t < g.nsteps; ++t) {
-      issue(t + R - 1);
-      cp_async_wait<R - 1>();
-      const int sl = t % R;
-      const unsigned char *st = stage + (size_t)sl * L.step;
-      const T *sr = reinterpret_cast<const T *>(st + L.rec) + tid;
-      const int *so = reinterpret_cast<const int *>(st + L.off) + tid;
-      const uint64_t *fs = fst + (size_t)sl * FS * W;
-      T *E = exB + (size_t)(t & 1) * NW * 32;
-      E[w * 32 + lane] = ym1[Q - 1];
-      __syncthreads();
-      // faces of this step: J (lane 0, one record per row, or per row pair
-      // in FP32) and K (warp 0, row 0); a stale staged copy is re-read from
-      // L2 (rare: one warp-uniform branch)
-      bool act[Q];
+    for (int t0 = 0; t0 < g.nsteps; t0 += R) {
+      static_for<0, R>([&](auto uc) {
+        constexpr int sl = decltype(uc)::value;
+        const int t = t0 + sl;
+        if (t >= g.nsteps) return;  // CTA-uniform
+        issue(t + R - 1, std::integral_constant<int, (sl + R - 1) % R>{});
+        cp_async_wait<R - 1>();
+        const unsigned char *st = stage + (size_t)sl * L.step;
+        const T *sr = reinterpret_cast<const T *>(st + L.rec) + tid;
+        const uint64_t *fs = fst + (size_t)sl * FS * W;
+        T *E = exB + (size_t)sl * NW * 32;
+        E[w * 32 + lane] = ym1[Q - 1];
+        __syncthreads();
+        // faces of this step: J (lane 0, one record per row, or per row pair
+        // in FP32) and K (warp 0, row 0); a stale staged copy is re-read from
+        // L2 (rare: one warp-uniform branch)
+        bool act[Q];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) act[q] = colq[q] && (unsigned)(t - tlo[q]) < nxu;
-      constexpr int NJ = Q / PJ;
-      bool needJ[NJ];
-      uint64_t jw[NJ][2], kw[2] = {0, 0};
-      bool stale = false;
+        for (int q = 0; q < Q; ++q) act[q] = colq[q] && (unsigned)(t - tlo[q]) < nxu;
+        constexpr int NJ = Q / PJ;
+        bool needJ[NJ];
+        uint64_t jw[NJ][2], kw[2] = {0, 0};
+        bool stale = false;
 #pragma unroll
-      for (int r = 0; r < NJ; ++r) {
-        const int q = r * PJ;
-        needJ[r] = lane == 0 && g.hasS && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]);
-        staged_words(fs + (w * Q + q) * W, jw[r]);
-        stale |= needJ[r] && !rec_ok<2>(jw[r], expect);
-      }
-      const bool needK = g.eB && g.hasB && act[0];
-      if (g.eB) {
-        staged_words(fs + (TK + lane) * W, kw);
-        stale |= needK && !rec_ok<2>(kw, expect);
-      }
-      if (__any_sync(0xffffffffu, stale)) {
+        for (int r = 0; r < NJ; ++r) {
+          const int q = r * PJ;
+          needJ[r] = lane == 0 && g.hasS && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]);
+          staged_words(fs + (w * Q + q) * W, jw[r]);
+          stale |= needJ[r] && !rec_ok<2>(jw[r], expect);
+        }
+        const bool needK = g.eB && g.hasB && act[0];
+        if (g.eB) {
+          staged_words(fs + (TK + lane) * W, kw);
+          stale |= needK && !rec_ok<2>(kw, expect);
+        }
+        if (__any_sync(0xffffffffu, stale)) {
 #pragma unroll
-        for (int r = 0; r < NJ; ++r)
-          if (needJ[r] && !rec_ok<2>(jw[r], expect))
-            face_wait<2>(upJ + ((long long)(t + kTJ - 1) * TK + w * Q + r * PJ) * W, expect, jw[r], c, abort, tr);
-        if (needK && !rec_ok<2>(kw, expect))
-          face_wait<2>(upK + kface + ((long long)(t + TK - 1) * kTJ + lane) * W, expect, kw, c, abort, tr);
-      }
-      const T yK = needK ? Face<T>::get(kw) : T(0);
-      T ny[Q];
+          for (int r = 0; r < NJ; ++r)
+            if (needJ[r] && !rec_ok<2>(jw[r], expect))
+              face_wait<2>(upJ + ((long long)(t + kTJ - 1) * TK + w * Q + r * PJ) * W, expect, jw[r], c, abort, tr);
+          if (needK && !rec_ok<2>(kw, expect))
+            face_wait<2>(upK + kface + ((long long)(t + TK - 1) * kTJ + lane) * W, expect, kw, c, abort, tr);
+        }
+        const T yK = needK ? Face<T>::get(kw) : T(0);
+        T ny[Q];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * RBY);
-        const T r = sr[q * NT];
-        T yS = shfl_up1(ym1[q]);
-        if (lane == 0) yS = (g.hasS && act[q]) ? face_row<T, PJ>(jw[q / PJ], q) : T(0);
-        T yB;
-        if (q > 0) yB = ym1[q > 0 ? q - 1 : 0];
-        else if (w > 0) yB = E[(w - 1) * 32 + lane];
-        else yB = yK;
-        T y = fma(-rec[REC_LB], yB, r);
-        y = fma(-rec[REC_LW], ym1[q], y);
-        y = fma(-rec[REC_LS], yS, y);
-        ny[q] = act[q] ? y * rec[REC_RLP] : T(0);
-      }
-      // stores last: y, then the face records (ordered memory operations)
+        for (int q = 0; q < Q; ++q) {
+          const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * RBY);
+          const T r = sr[q * NT];
+          T yS = shfl_up1(ym1[q]);
+          if (lane == 0) yS = (g.hasS && act[q]) ? face_row<T, PJ>(jw[q / PJ], q) : T(0);
+          T yB;
+          if (q > 0) yB = ym1[q > 0 ? q - 1 : 0];
+          else if (w > 0) yB = E[(w - 1) * 32 + lane];
+          else yB = yK;
+          T y = fma(-rec[REC_LB], yB, r);
+          y = fma(-rec[REC_LW], ym1[q], y);
+          y = fma(-rec[REC_LS], yS, y);
+          ny[q] = act[q] ? y * rec[REC_RLP] : T(0);
+        }
+        // stores last: y, then the face records (ordered memory operations)
 #pragma unroll
-      for (int q = 0; q < Q; ++q)
-        if (act[q]) yb[so[q * NT]] = ny[q];
+        for (int q = 0; q < Q; ++q)
+          if (act[q]) yb[offr[sl][q]] = ny[q];
 #pragma unroll
-      for (int q = 0; q < Q; q += PJ)
-        face_put<T, PJ>(pjn + q * W, ny, q, ep, lane == kTJ - 1 && g.hasN && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]));
-      if (g.eT)  // warp-uniform
-        Face<T>::put_if(pkn, ny[Q - 1], ep, g.hasT && act[Q - 1]);
-      pjn += (long long)TK * W;
-      pkn += (long long)kTJ * W;
+        for (int q = 0; q < Q; q += PJ)
+          face_put<T, PJ>(pjn + q * W, ny, q, ep, lane == kTJ - 1 && g.hasN && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]));
+        if (g.eT)  // warp-uniform
+          Face<T>::put_if(pkn, ny[Q - 1], ep, g.hasT && act[Q - 1]);
+        pjn += (long long)TK * W;
+        pkn += (long long)kTJ * W;
 #pragma unroll
-      for (int q = 0; q < Q; ++q) ym1[q] = ny[q];
+        for (int q = 0; q < Q; ++q) ym1[q] = ny[q];
+      });
     }
     cp_async_wait<0>();
     if (tr && threadIdx.x == 0) tr[2] = gtimer();
@@ -601,7 +612,7 @@ __global__ void __launch_bounds__(512, 1) k_backward(BwdParams<T> P) {
   const SweepLayout L = bwd_layout((int)sizeof(T), ZX, Q, R, NT, c.tab_ints);
   int *sPO = reinterpret_cast<int *>(smem_raw);
   unsigned char *stage = smem_raw + L.tab;
-  T *exT = reinterpret_cast<T *>(stage + (size_t)R * L.step);  // [2][NW][32]: d of a warp's first row
+  T *exT = reinterpret_cast<T *>(stage + (size_t)R * L.step);  // [R][NW][32]: d of a warp's first row
   uint64_t *fst = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(exT) + L.exch);
   const int FS = L.fs;
   bool abort = false;
@@ -650,35 +661,35 @@ __global__ void __launch_bounds__(512, 1) k_backward(BwdParams<T> P) {
     uint64_t *pjn = myf + ((long long)last * TK + w * Q) * W;
     uint64_t *pkn = myf + kface + ((long long)last * kTJ + lane) * W;
 
-    auto issue = [&](int uu) {
+    // slots as in the forward sweep: stage, exchange and offsets of step u
+    // at u % R, the loop unrolled by R
+    int offr[R][Q];
+    auto issue = [&](int uu, auto slot) {
+      constexpr int sl = decltype(slot)::value;
       if (uu < g.nsteps) {
         if (uu - cb >= C) {
           cb += C;
           chunk = rowbase_chunk<Q>(B, sPO, sF, g.s0, kchunk, last - (cb + lane / Q), g.nsteps);
         }
         const int t = last - uu;
-        const int sl = uu % R;
         unsigned char *st = stage + (size_t)sl * L.step;
         T *sc = reinterpret_cast<T *>(st + L.rec) + tid;
-        int *so = reinterpret_cast<int *>(st + L.off) + tid;
         uint64_t *fs = fst + (size_t)sl * FS * W;
-        int off[Q];
         bool v[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          off[q] = __shfl_sync(0xffffffffu, chunk, (uu - cb) * Q + q) + g.j;
+          offr[sl][q] = __shfl_sync(0xffffffffu, chunk, (uu - cb) * Q + q) + g.j;
           v[q] = colq[q] && (unsigned)(t - tlo[q]) < nxu;
         }
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          const int o = v[q] ? off[q] : 0;
+          const int o = v[q] ? offr[sl][q] : 0;
           unsigned char *d = st + ((size_t)q * NT + tid) * RBY;
           const unsigned char *src = reinterpret_cast<const unsigned char *>(recb + (size_t)o * 4);
 #pragma unroll
           for (int z = 0; z < RBY / 16; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v[q]);
           cp_async_zfill<sizeof(T)>(sc + (SY + q) * NT, yb + o, v[q]);
           if constexpr (!ZX) cp_async_zfill<sizeof(T)>(sc + (SX + q) * NT, xb + o, v[q]);
-          so[q * NT] = off[q];
         }
 #pragma unroll
         for (int q = 0; q < Q; q += PJ) {
@@ -692,84 +703,86 @@ __global__ void __launch_bounds__(512, 1) k_backward(BwdParams<T> P) {
       }
       cp_async_commit();
     };
-#pragma unroll
-    for (int uu = 0; uu < R - 1; ++uu) issue(uu);
+    static_for<0, R - 1>([&](auto u) { issue(decltype(u)::value, u); });
 
     T dE[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) dE[q] = T(0);
-    for (int u = 0; u < g.nsteps; ++u) {
-      issue(u + R - 1);
-      cp_async_wait<R - 1>();
-      const int sl = u % R;
-      const unsigned char *st = stage + (size_t)sl * L.step;
-      const T *sc = reinterpret_cast<const T *>(st + L.rec) + tid;
-      const int *so = reinterpret_cast<const int *>(st + L.off) + tid;
-      const uint64_t *fs = fst + (size_t)sl * FS * W;
-      const int t = last - u;
-      T *E = exT + (size_t)(u & 1) * NW * 32;
-      E[w * 32 + lane] = dE[0];
-      __syncthreads();
-      // faces of this step: J (lane 31, per row or row pair) and K (last warp, last row)
-      bool act[Q];
+    for (int u0 = 0; u0 < g.nsteps; u0 += R) {
+      static_for<0, R>([&](auto uc) {
+        constexpr int sl = decltype(uc)::value;
+        const int u = u0 + sl;
+        if (u >= g.nsteps) return;  // CTA-uniform
+        issue(u + R - 1, std::integral_constant<int, (sl + R - 1) % R>{});
+        cp_async_wait<R - 1>();
+        const unsigned char *st = stage + (size_t)sl * L.step;
+        const T *sc = reinterpret_cast<const T *>(st + L.rec) + tid;
+        const uint64_t *fs = fst + (size_t)sl * FS * W;
+        const int t = last - u;
+        T *E = exT + (size_t)sl * NW * 32;
+        E[w * 32 + lane] = dE[0];
+        __syncthreads();
+        // faces of this step: J (lane 31, per row or row pair) and K (last warp, last row)
+        bool act[Q];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) act[q] = colq[q] && (unsigned)(t - tlo[q]) < nxu;
-      constexpr int NJ = Q / PJ;
-      bool needJ[NJ];
-      uint64_t jw[NJ][2], kw[2] = {0, 0};
-      bool stale = false;
+        for (int q = 0; q < Q; ++q) act[q] = colq[q] && (unsigned)(t - tlo[q]) < nxu;
+        constexpr int NJ = Q / PJ;
+        bool needJ[NJ];
+        uint64_t jw[NJ][2], kw[2] = {0, 0};
+        bool stale = false;
 #pragma unroll
-      for (int r = 0; r < NJ; ++r) {
-        const int q = r * PJ;
-        needJ[r] = lane == kTJ - 1 && g.hasN && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]);
-        staged_words(fs + (w * Q + q) * W, jw[r]);
-        stale |= needJ[r] && !rec_ok<2>(jw[r], expect);
-      }
-      const bool needK = g.eT && g.hasT && act[Q - 1];
-      if (g.eT) {
-        staged_words(fs + (TK + lane) * W, kw);
-        stale |= needK && !rec_ok<2>(kw, expect);
-      }
-      if (__any_sync(0xffffffffu, stale)) {
+        for (int r = 0; r < NJ; ++r) {
+          const int q = r * PJ;
+          needJ[r] = lane == kTJ - 1 && g.hasN && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]);
+          staged_words(fs + (w * Q + q) * W, jw[r]);
+          stale |= needJ[r] && !rec_ok<2>(jw[r], expect);
+        }
+        const bool needK = g.eT && g.hasT && act[Q - 1];
+        if (g.eT) {
+          staged_words(fs + (TK + lane) * W, kw);
+          stale |= needK && !rec_ok<2>(kw, expect);
+        }
+        if (__any_sync(0xffffffffu, stale)) {
 #pragma unroll
-        for (int r = 0; r < NJ; ++r)
-          if (needJ[r] && !rec_ok<2>(jw[r], expect))
-            face_wait<2>(dnJ + ((long long)(t - (kTJ - 1)) * TK + w * Q + r * PJ) * W, expect, jw[r], c, abort, tr);
-        if (needK && !rec_ok<2>(kw, expect))
-          face_wait<2>(dnK + kface + ((long long)(t - (TK - 1)) * kTJ + lane) * W, expect, kw, c, abort, tr);
-      }
-      const T dK = needK ? Face<T>::get(kw) : T(0);
-      T nd[Q], xv[Q];
+          for (int r = 0; r < NJ; ++r)
+            if (needJ[r] && !rec_ok<2>(jw[r], expect))
+              face_wait<2>(dnJ + ((long long)(t - (kTJ - 1)) * TK + w * Q + r * PJ) * W, expect, jw[r], c, abort, tr);
+          if (needK && !rec_ok<2>(kw, expect))
+            face_wait<2>(dnK + kface + ((long long)(t - (TK - 1)) * kTJ + lane) * W, expect, kw, c, abort, tr);
+        }
+        const T dK = needK ? Face<T>::get(kw) : T(0);
+        T nd[Q], xv[Q];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * RBY);
-        T dN = shfl_dn1(dE[q]);
-        if (lane == kTJ - 1) dN = (g.hasN && act[q]) ? face_row<T, PJ>(jw[q / PJ], q) : T(0);
-        T dT;
-        if (q < Q - 1) dT = dE[q < Q - 1 ? q + 1 : 0];
-        else if (w < NW - 1) dT = E[(w + 1) * 32 + lane];
-        else dT = dK;
-        T d = fma(-rec[RECB_UE], dE[q], sc[(SY + q) * NT]);
-        d = fma(-rec[RECB_UN], dN, d);
-        d = fma(-rec[RECB_UT], dT, d);
-        T xn = d;
-        if constexpr (!ZX) xn = sc[(SX + q) * NT] + d;
-        xv[q] = xn;
-        nd[q] = act[q] ? d : T(0);
-      }
-      // stores last: the update, then the face records (ordered memory operations)
+        for (int q = 0; q < Q; ++q) {
+          const T *rec = reinterpret_cast<const T *>(st + ((size_t)q * NT + tid) * RBY);
+          T dN = shfl_dn1(dE[q]);
+          if (lane == kTJ - 1) dN = (g.hasN && act[q]) ? face_row<T, PJ>(jw[q / PJ], q) : T(0);
+          T dT;
+          if (q < Q - 1) dT = dE[q < Q - 1 ? q + 1 : 0];
+          else if (w < NW - 1) dT = E[(w + 1) * 32 + lane];
+          else dT = dK;
+          T d = fma(-rec[RECB_UE], dE[q], sc[(SY + q) * NT]);
+          d = fma(-rec[RECB_UN], dN, d);
+          d = fma(-rec[RECB_UT], dT, d);
+          T xn = d;
+          if constexpr (!ZX) xn = sc[(SX + q) * NT] + d;
+          xv[q] = xn;
+          nd[q] = act[q] ? d : T(0);
+        }
+        // stores last: the update, then the face records (ordered memory operations)
 #pragma unroll
-      for (int q = 0; q < Q; ++q)
-        if (act[q]) xb[so[q * NT]] = xv[q];
+        for (int q = 0; q < Q; ++q)
+          if (act[q]) xb[offr[sl][q]] = xv[q];
 #pragma unroll
-      for (int q = 0; q < Q; q += PJ)
-        face_put<T, PJ>(pjn + q * W, nd, q, ep, lane == 0 && g.hasS && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]));
-      if (g.eB)  // warp-uniform
-        Face<T>::put_if(pkn, nd[0], ep, g.hasB && act[0]);
-      pjn -= (long long)TK * W;
-      pkn -= (long long)kTJ * W;
+        for (int q = 0; q < Q; q += PJ)
+          face_put<T, PJ>(pjn + q * W, nd, q, ep, lane == 0 && g.hasS && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]));
+        if (g.eB)  // warp-uniform
+          Face<T>::put_if(pkn, nd[0], ep, g.hasB && act[0]);
+        pjn -= (long long)TK * W;
+        pkn -= (long long)kTJ * W;
 #pragma unroll
-      for (int q = 0; q < Q; ++q) dE[q] = nd[q];
+        for (int q = 0; q < Q; ++q) dE[q] = nd[q];
+      });
     }
     cp_async_wait<0>();
     if (tr && threadIdx.x == 0) tr[2] = gtimer();
