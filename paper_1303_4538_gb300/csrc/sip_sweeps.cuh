@@ -73,6 +73,27 @@ __device__ __forceinline__ void cp_async_16_l2(void *sdst, const void *gsrc, boo
                "r"(valid ? 16 : 0)
                : "memory");
 }
+// The same copies without a compiler memory clobber, for the substitution
+// sweeps: there a stage slot is written only by these copies and read only
+// after the step's cp.async.wait_group (which keeps its clobber) and CTA
+// barrier, and every step ends with the face stores (asm with a clobber,
+// executed by every thread), so no load of a slot can move past the copy
+// that refills it.  Without the clobber the compiler may interleave the
+// next stage's address arithmetic with the current step's shared loads.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_zfill_nc(void *sdst, const void *gsrc, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_u32(sdst)), "l"(gsrc), "n"(BYTES),
+               "r"(valid ? BYTES : 0));
+}
+__device__ __forceinline__ void cp_async_16_l2_nc(void *sdst, const void *gsrc, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(sdst)), "l"(gsrc),
+               "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_16_if_nc(void *sdst, const void *gsrc, bool pred) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q cp.async.cg.shared.global [%0], [%1], 16;\n}\n" ::"r"(
+                   smem_u32(sdst)),
+               "l"(gsrc), "r"((int)pred));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -252,6 +273,17 @@ __device__ __forceinline__ void staged_words(const uint64_t *staged, uint64_t (&
   const ulonglong2 s2 = *reinterpret_cast<const ulonglong2 *>(staged);
   w[0] = s2.x;
   w[1] = s2.y;
+}
+
+// The same, only where `pred` holds (zero words elsewhere): a predicated
+// load instead of a branch around it.
+__device__ __forceinline__ void staged_words_if(const uint64_t *staged, uint64_t (&w)[2], bool pred) {
+  unsigned long long a = 0, b = 0;
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %3, 0;\n @p ld.shared.v2.u64 {%0, %1}, [%2];\n}\n"
+               : "+l"(a), "+l"(b)
+               : "r"(smem_u32(staged)), "r"((int)pred));
+  w[0] = a;
+  w[1] = b;
 }
 
 // Row bases of a warp's Q rows for C = 32 / Q consecutive steps, one per
@@ -454,12 +486,15 @@ __global__ void __launch_bounds__(512, 1) k_forward(FwdParams<T> P) {
     const T *recb = P.rec + B.cell0 * 4;
     const T *rb = P.r + B.cell0;
     T *yb = P.y + B.cell0;
-    // running face pointers: records read by the copies of issue step tt and
-    // written at compute step t (row slot w Q; K slot lane)
-    const uint64_t *fjn = upJ + ((long long)(kTJ - 1) * TK + w * Q) * W;
-    const uint64_t *fkn = upK + kface + ((long long)(TK - 1) * kTJ + lane) * W;
-    uint64_t *pjn = myf + (long long)w * Q * W;
-    uint64_t *pkn = myf + kface + (long long)lane * W;
+    // face records read by the copies of issue step tt (the producers' steps
+    // tt + kTJ - 1 and tt + TK - 1) and written at compute step t (row slot
+    // w Q; K slot lane): per-tile bases plus 32-bit step offsets, computed
+    // from the step (no pointer carried from step to step)
+    const uint64_t *fjb = upJ + ((long long)(kTJ - 1) * TK + w * Q) * W;
+    const uint64_t *fkb = upK + kface + ((long long)(TK - 1) * kTJ + lane) * W;
+    uint64_t *pjb = myf + (long long)w * Q * W;
+    uint64_t *pkb = myf + kface + (long long)lane * W;
+    const int TKW = TK * W, TJW = kTJ * W;
 
     // Step t uses stage slot, exchange slot and store-offset registers
     // t % R: the step loop is unrolled by R, so every slot index is a
@@ -467,7 +502,8 @@ __global__ void __launch_bounds__(512, 1) k_forward(FwdParams<T> P) {
     int offr[R][Q];
     auto issue = [&](int tt, auto slot) {
       constexpr int sl = decltype(slot)::value;
-      if (tt < g.nsteps) {
+      // past the last step every copy is predicated off (no cell is valid)
+      {
         if (tt - cb >= C) {
           cb += C;
           chunk = rowbase_chunk<Q>(B, sPO, sF, g.s0, kchunk, cb + lane / Q, g.nsteps);
@@ -488,18 +524,15 @@ __global__ void __launch_bounds__(512, 1) k_forward(FwdParams<T> P) {
           unsigned char *d = st + ((size_t)q * NT + tid) * RBY;
           const unsigned char *src = reinterpret_cast<const unsigned char *>(recb + (size_t)o * 4);
 #pragma unroll
-          for (int z = 0; z < RBY / 16; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v[q]);
-          cp_async_zfill<sizeof(T)>(sr + q * NT, rb + o, v[q]);
+          for (int z = 0; z < RBY / 16; ++z) cp_async_16_l2_nc(d + 16 * z, src + 16 * z, v[q]);
+          cp_async_zfill_nc<sizeof(T)>(sr + q * NT, rb + o, v[q]);
         }
 #pragma unroll
         for (int q = 0; q < Q; q += PJ) {
           const bool vq = PJ == 2 ? (v[q] || v[q + PJ - 1]) : v[q];
-          cp_async_16_if(fs + (w * Q + q) * W, fjn + q * W, lane == 0 && g.hasS && vq);
+          cp_async_16_if_nc(fs + (w * Q + q) * W, fjb + tt * TKW + q * W, lane == 0 && g.hasS && vq);
         }
-        if (g.eB)  // warp-uniform
-          cp_async_16_if(fs + (TK + lane) * W, fkn, g.hasB && v[0]);
-        fjn += (long long)TK * W;
-        fkn += (long long)kTJ * W;
+        cp_async_16_if_nc(fs + (TK + lane) * W, fkb + tt * TJW, g.eB && g.hasB && v[0]);
       }
       cp_async_commit();
     };
@@ -508,11 +541,13 @@ __global__ void __launch_bounds__(512, 1) k_forward(FwdParams<T> P) {
     T ym1[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) ym1[q] = T(0);
+    // the walk is padded to a multiple of R steps: the extra steps touch no
+    // cell (every copy, store and face store is predicated off), so the
+    // unrolled body needs no exit test
     for (int t0 = 0; t0 < g.nsteps; t0 += R) {
       static_for<0, R>([&](auto uc) {
         constexpr int sl = decltype(uc)::value;
         const int t = t0 + sl;
-        if (t >= g.nsteps) return;  // CTA-uniform
         issue(t + R - 1, std::integral_constant<int, (sl + R - 1) % R>{});
         cp_async_wait<R - 1>();
         const unsigned char *st = stage + (size_t)sl * L.step;
@@ -539,10 +574,8 @@ __global__ void __launch_bounds__(512, 1) k_forward(FwdParams<T> P) {
           stale |= needJ[r] && !rec_ok<2>(jw[r], expect);
         }
         const bool needK = g.eB && g.hasB && act[0];
-        if (g.eB) {
-          staged_words(fs + (TK + lane) * W, kw);
-          stale |= needK && !rec_ok<2>(kw, expect);
-        }
+        staged_words_if(fs + (TK + lane) * W, kw, g.eB);
+        stale |= needK && !rec_ok<2>(kw, expect);
         if (__any_sync(0xffffffffu, stale)) {
 #pragma unroll
           for (int r = 0; r < NJ; ++r)
@@ -574,11 +607,9 @@ __global__ void __launch_bounds__(512, 1) k_forward(FwdParams<T> P) {
           if (act[q]) yb[offr[sl][q]] = ny[q];
 #pragma unroll
         for (int q = 0; q < Q; q += PJ)
-          face_put<T, PJ>(pjn + q * W, ny, q, ep, lane == kTJ - 1 && g.hasN && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]));
-        if (g.eT)  // warp-uniform
-          Face<T>::put_if(pkn, ny[Q - 1], ep, g.hasT && act[Q - 1]);
-        pjn += (long long)TK * W;
-        pkn += (long long)kTJ * W;
+          face_put<T, PJ>(pjb + t * TKW + q * W, ny, q, ep,
+                          lane == kTJ - 1 && g.hasN && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]));
+        Face<T>::put_if(pkb + t * TJW, ny[Q - 1], ep, g.eT && g.hasT && act[Q - 1]);
 #pragma unroll
         for (int q = 0; q < Q; ++q) ym1[q] = ny[q];
       });
@@ -654,19 +685,24 @@ __global__ void __launch_bounds__(512, 1) k_backward(BwdParams<T> P) {
     const T *recb = P.rec + B.cell0 * 4;
     const T *yb = P.y + B.cell0;
     T *xb = P.x + B.cell0;
-    // running face pointers (descending planes): the records read by the
-    // copies of issue step uu (plane last - uu) and written at step u
-    const uint64_t *fjn = dnJ + ((long long)(last - (kTJ - 1)) * TK + w * Q) * W;
-    const uint64_t *fkn = dnK + kface + ((long long)(last - (TK - 1)) * kTJ + lane) * W;
-    uint64_t *pjn = myf + ((long long)last * TK + w * Q) * W;
-    uint64_t *pkn = myf + kface + ((long long)last * kTJ + lane) * W;
+    // face records (descending planes) read by the copies of issue step uu
+    // (plane t = last - uu: the producers' steps t - (kTJ - 1) and
+    // t - (TK - 1)) and written at step u (plane last - u): per-tile bases
+    // plus 32-bit step offsets (negative past the walk's end, where every
+    // copy and store is predicated off)
+    const uint64_t *fjb = dnJ + ((long long)(-(kTJ - 1)) * TK + w * Q) * W;
+    const uint64_t *fkb = dnK + kface + ((long long)(-(TK - 1)) * kTJ + lane) * W;
+    uint64_t *pjb = myf + (long long)w * Q * W;
+    uint64_t *pkb = myf + kface + (long long)lane * W;
+    const int TKW = TK * W, TJW = kTJ * W;
 
     // slots as in the forward sweep: stage, exchange and offsets of step u
     // at u % R, the loop unrolled by R
     int offr[R][Q];
     auto issue = [&](int uu, auto slot) {
       constexpr int sl = decltype(slot)::value;
-      if (uu < g.nsteps) {
+      // past the last step every copy is predicated off (no cell is valid)
+      {
         if (uu - cb >= C) {
           cb += C;
           chunk = rowbase_chunk<Q>(B, sPO, sF, g.s0, kchunk, last - (cb + lane / Q), g.nsteps);
@@ -687,19 +723,16 @@ __global__ void __launch_bounds__(512, 1) k_backward(BwdParams<T> P) {
           unsigned char *d = st + ((size_t)q * NT + tid) * RBY;
           const unsigned char *src = reinterpret_cast<const unsigned char *>(recb + (size_t)o * 4);
 #pragma unroll
-          for (int z = 0; z < RBY / 16; ++z) cp_async_16_l2(d + 16 * z, src + 16 * z, v[q]);
-          cp_async_zfill<sizeof(T)>(sc + (SY + q) * NT, yb + o, v[q]);
-          if constexpr (!ZX) cp_async_zfill<sizeof(T)>(sc + (SX + q) * NT, xb + o, v[q]);
+          for (int z = 0; z < RBY / 16; ++z) cp_async_16_l2_nc(d + 16 * z, src + 16 * z, v[q]);
+          cp_async_zfill_nc<sizeof(T)>(sc + (SY + q) * NT, yb + o, v[q]);
+          if constexpr (!ZX) cp_async_zfill_nc<sizeof(T)>(sc + (SX + q) * NT, xb + o, v[q]);
         }
 #pragma unroll
         for (int q = 0; q < Q; q += PJ) {
           const bool vq = PJ == 2 ? (v[q] || v[q + PJ - 1]) : v[q];
-          cp_async_16_if(fs + (w * Q + q) * W, fjn + q * W, lane == kTJ - 1 && g.hasN && vq);
+          cp_async_16_if_nc(fs + (w * Q + q) * W, fjb + t * TKW + q * W, lane == kTJ - 1 && g.hasN && vq);
         }
-        if (g.eT)  // warp-uniform
-          cp_async_16_if(fs + (TK + lane) * W, fkn, g.hasT && v[Q - 1]);
-        fjn -= (long long)TK * W;
-        fkn -= (long long)kTJ * W;
+        cp_async_16_if_nc(fs + (TK + lane) * W, fkb + t * TJW, g.eT && g.hasT && v[Q - 1]);
       }
       cp_async_commit();
     };
@@ -708,11 +741,11 @@ __global__ void __launch_bounds__(512, 1) k_backward(BwdParams<T> P) {
     T dE[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) dE[q] = T(0);
+    // walk padded to a multiple of R steps, as in the forward sweep
     for (int u0 = 0; u0 < g.nsteps; u0 += R) {
       static_for<0, R>([&](auto uc) {
         constexpr int sl = decltype(uc)::value;
         const int u = u0 + sl;
-        if (u >= g.nsteps) return;  // CTA-uniform
         issue(u + R - 1, std::integral_constant<int, (sl + R - 1) % R>{});
         cp_async_wait<R - 1>();
         const unsigned char *st = stage + (size_t)sl * L.step;
@@ -738,10 +771,8 @@ __global__ void __launch_bounds__(512, 1) k_backward(BwdParams<T> P) {
           stale |= needJ[r] && !rec_ok<2>(jw[r], expect);
         }
         const bool needK = g.eT && g.hasT && act[Q - 1];
-        if (g.eT) {
-          staged_words(fs + (TK + lane) * W, kw);
-          stale |= needK && !rec_ok<2>(kw, expect);
-        }
+        staged_words_if(fs + (TK + lane) * W, kw, g.eT);
+        stale |= needK && !rec_ok<2>(kw, expect);
         if (__any_sync(0xffffffffu, stale)) {
 #pragma unroll
           for (int r = 0; r < NJ; ++r)
@@ -775,11 +806,9 @@ __global__ void __launch_bounds__(512, 1) k_backward(BwdParams<T> P) {
           if (act[q]) xb[offr[sl][q]] = xv[q];
 #pragma unroll
         for (int q = 0; q < Q; q += PJ)
-          face_put<T, PJ>(pjn + q * W, nd, q, ep, lane == 0 && g.hasS && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]));
-        if (g.eB)  // warp-uniform
-          Face<T>::put_if(pkn, nd[0], ep, g.hasB && act[0]);
-        pjn -= (long long)TK * W;
-        pkn -= (long long)kTJ * W;
+          face_put<T, PJ>(pjb + t * TKW + q * W, nd, q, ep,
+                          lane == 0 && g.hasS && (PJ == 2 ? (act[q] || act[q + PJ - 1]) : act[q]));
+        Face<T>::put_if(pkb + t * TJW, nd[0], ep, g.eB && g.hasB && act[0]);
 #pragma unroll
         for (int q = 0; q < Q; ++q) dE[q] = nd[q];
       });
