@@ -323,13 +323,17 @@ def run_gb300(args):
     desc = sip.make_desc(blk.nx, blk.ny, blk.nz, [A[0], None, A[2], None, A[4], None, A[6]], b, x, symmetric=True)
 
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # tile shapes from the autotuner (plan creation, untimed)
+    opt_r = tuned_options(ctx, [desc], mode=sip.SIP_MODE_F32_REFINED, inner_iters=args.inner)
+    opt_d = tuned_options(ctx, [desc], mode=sip.SIP_MODE_F64)
+    torch.cuda.synchronize()
     e0.record(stream)
-    plan_r = sip.Plan(ctx, [desc], sip.default_options(mode=sip.SIP_MODE_F32_REFINED, inner_iters=args.inner))
+    plan_r = sip.Plan(ctx, [desc], opt_r)
     e1.record(stream)
     torch.cuda.synchronize()
     factor_ms_r = e0.elapsed_time(e1)
     e0.record(stream)
-    plan_d = sip.Plan(ctx, [desc], sip.default_options(mode=sip.SIP_MODE_F64))
+    plan_d = sip.Plan(ctx, [desc], opt_d)
     e1.record(stream)
     torch.cuda.synchronize()
     factor_ms_d = e0.elapsed_time(e1)
@@ -395,8 +399,10 @@ def run_gb300(args):
         # the refined form with other numbers of FP32 iterations per FP64 correction
         for m in (1, 2, 4, 8):
             if m != args.inner and not args.no_inner_sweep:
-                runs.append((f"f32_refined_m{m}", sip.Plan(ctx, [desc], sip.default_options(
-                    mode=sip.SIP_MODE_F32_REFINED, inner_iters=m)), m, True))
+                om = sip.default_options(mode=sip.SIP_MODE_F32_REFINED, inner_iters=m,
+                                         rows_per_thread=opt_r.rows_per_thread, tile_k=opt_r.tile_k,
+                                         stages=opt_r.stages)
+                runs.append((f"f32_refined_m{m}", sip.Plan(ctx, [desc], om), m, True))
         for name, plan, inner, own in runs:
             barrier()
             x.zero_()
@@ -462,7 +468,8 @@ def run_gb300(args):
         "config": {"workload": f"poisson_{args.n}cube", "cells": N, "alpha": 0.92, "mode": "f32_refined",
                    "inner_iters": args.inner, "corrections_per_step": args.iters,
                    "stop_rule": "none: a fixed number of corrections per step (rtol 0)",
-                   "tile": dict(zip(("rows_per_thread", "tile_k", "stages"), plan_r.shape())),
+                   "tile": dict(zip(("rows_per_thread", "tile_k", "stages"), plan_r.shape()),
+                                source="measuring autotuner (sip_options.autotune), at plan creation"),
                    "parallelism": f"replicas x{world}", "l2": "working set > L2 (plan arrays "
                    f"{plan_r.nbytes() / 1e9:.2f} GB)", "step": "sip_solve on the factored plan, x reset to 0"},
         "roofline": roofline(prof_r),
@@ -473,7 +480,8 @@ def run_gb300(args):
         "gpu_launches": int(launches_r),
         "clocks": clk,
         "fp64": {"value": round(val_d, 1), "unit": "MLUP/s", "ms_per_step": round(ms_d / args.steps, 3),
-                 "gpu_launches": int(launches_d), "roofline": roofline(prof_d)},
+                 "gpu_launches": int(launches_d), "roofline": roofline(prof_d),
+                 "tile": dict(zip(("rows_per_thread", "tile_k", "stages"), plan_d.shape()))},
         "factor_ms": {"f32_refined": round(factor_ms_r, 2), "f64": round(factor_ms_d, 2)},
         "kernel_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in prof_r.items()},
         "kernel_ms_fp64": {k: round(v[0] / max(v[1], 1), 4) for k, v in prof_d.items()},
@@ -496,6 +504,19 @@ def run_gb300(args):
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def tuned_options(ctx, descs, ifaces=None, **kw):
+    """Options carrying the tile shape that the library's measuring autotuner
+    picks for these blocks (one throw-away tuned plan, built outside every
+    timed region), so that plans built from them time their factorisation
+    alone."""
+    from paper_1303_4538_gb300 import sip
+    o = sip.default_options(autotune=1, **kw)
+    p = sip.Plan(ctx, descs, o, ifaces=ifaces) if ifaces else sip.Plan(ctx, descs, o)
+    q, tk, r = p.shape()
+    p.close()
+    return sip.default_options(rows_per_thread=q, tile_k=tk, stages=r, **kw)
 
 
 def _solve_timed(plan, x, stream, rtol, max_iters, reps=1):
@@ -576,7 +597,7 @@ def large(args, local):
     x = torch.zeros(blk.n, dtype=torch.float64, device="cuda")
     desc = sip.make_desc(blk.nx, blk.ny, blk.nz, A, b, x, coef_dtype=1)
     out = {"workload": "convdiff_pe10_384cube", "cells": blk.n, "coefficients": "f32"}
-    plan = sip.Plan(ctx, [desc], sip.default_options(mode=sip.SIP_MODE_F32_REFINED, alpha=0.5, graphs=1))
+    plan = sip.Plan(ctx, [desc], tuned_options(ctx, [desc], mode=sip.SIP_MODE_F32_REFINED, alpha=0.5, graphs=1))
     ms, it, rel, conv = _solve_timed(plan, x, stream, 1e-8, 3000)
     import numpy as np
     xs = x.cpu().numpy()
@@ -596,14 +617,16 @@ def large(args, local):
     out["f32_refined_alpha05"]["relres_fp64_A64"] = rn64 / bn64
     del x_ref
     desc = sip.make_desc(blk.nx, blk.ny, blk.nz, A, b, x)
-    plan = sip.Plan(ctx, [desc], sip.default_options(mode=sip.SIP_MODE_F64, alpha=0.5, graphs=1))
+    opt64 = tuned_options(ctx, [desc], mode=sip.SIP_MODE_F64, alpha=0.5, graphs=1)
+    plan = sip.Plan(ctx, [desc], opt64)
     ms, it, rel, conv = _solve_timed(plan, x, stream, 1e-8, 5000)
     xs = x.cpu().numpy()
     out["f64_alpha05"] = {"seconds": round(ms / 1e3, 3), "iterations": it, "relres": rel, "converged": bool(conv),
                           "coefficients": "f64",
                           "err_vs_xstar": float(np.linalg.norm(xs - blk.xstar) / np.linalg.norm(blk.xstar))}
     plan.close()
-    plan = sip.Plan(ctx, [desc], sip.default_options(mode=sip.SIP_MODE_F64, alpha=0.92, graphs=1))
+    opt64.alpha = 0.92
+    plan = sip.Plan(ctx, [desc], opt64)
     x.zero_()
     plan.iterate(40)
     h = plan.history()

@@ -634,7 +634,7 @@ ShapeChoice choose_shape(sip_ctx *ctx, const std::vector<BlockHost> &blocks, con
 // fastest plan is kept.  With SIP_AUTOTUNE_CACHE naming a file, results are
 // read from and appended to it, one line per problem signature:
 //   <signature> <rows_per_thread> <tile_k> <stages> <ms per sweep pair>
-constexpr int kTuneCandidates = 3;
+constexpr int kTuneCandidates = 4;
 constexpr int kTuneReps = 3;
 std::mutex g_tune_mu;
 
