@@ -58,7 +58,8 @@ def test_iterations_match_oracle(shape, kind):
 
 @pytest.mark.parametrize("tile", [(32, 2), (32, 4), (32, 6), (32, 8), (32, 12), (32, 8, 2), (32, 8, 4),
                                   (32, 16, 4), (32, 20, 4), (32, 32, 2), (32, 32, 4), (32, 8, 2, 4),
-                                  (32, 16, 2, 6), (32, 12, 4, 3)])
+                                  (32, 16, 2, 6), (32, 12, 4, 3), (32, 8, 1), (32, 6, 1, 4), (32, 10, 1, 6),
+                                  (32, 16, 1, 3)])
 def test_tile_shapes_agree(tile):
     """(tile_j, tile_k[, rows_per_thread[, stages]]): every column-tile shape
     and prefetch depth gives the oracle's iterates (the 32 x 32 tiles factor
