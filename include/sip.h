@@ -117,9 +117,9 @@ typedef struct {
                               context's stream (one replay per 16 iterations; needs a
                               non-NULL stream, ignored while profiling); 0: launch by launch */
   int32_t rows_per_thread; /* rows of a column tile each sweep thread walks (the tile is
-                              32 x rows_per_thread * warps): 0 (auto), 2 or 4 */
+                              32 x rows_per_thread * warps): 0 (auto: 1 or 2), 1, 2 or 4 */
   int32_t autotune;        /* 1 (with tile_k, rows_per_thread and stages all 0): sip_factor builds
-                              the cost model's best few tile shapes, times their forward +
+                              the launch model's best four tile shapes (sip_tile_model), times their forward +
                               backward sweeps on the plan's own work vectors and keeps the
                               fastest plan; with the environment variable SIP_AUTOTUNE_CACHE
                               naming a file, a result for the same signature (GPU SM count,
