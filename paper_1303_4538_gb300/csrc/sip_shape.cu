@@ -11,10 +11,11 @@
 // w the warps per SM sub-partition of all tiles then active on its SM (the
 // average over the tile's lifetime, solved by a short fixed-point
 // iteration).  a and b were fitted on GB300 to the launches of 256^3, 192^3
-// and 128^3 Poisson blocks for every shape with one and two rows per thread;
-// the model's first choice was within 4 % of the fastest measured shape on
-// those blocks, the 64-block mesh and the 384^3 block, and the fastest shape
-// was always among its first three.
+// and 128^3 Poisson blocks for every shape with one and two rows per thread.
+// Measured against the fastest shape of each launch (128^3, 256^3, the
+// 64-block mesh; FP32 and FP64 sweeps) its first choice is the fastest or
+// within 7 % (15 % for the FP64 mesh), and the fastest shape is always among
+// its first three, which the autotuner then times.
 #include <algorithm>
 #include <cmath>
 #include <queue>
